@@ -1,0 +1,353 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU needed).
+
+Each test names the passage it pins and the mistake it would catch.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg
+import scipy.ndimage
+import scipy.special
+
+import oracle
+from paper_2212_08058_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_counts.txt")
+
+
+def _golden():
+    rows = {}
+    with open(GOLDEN) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            key, *vals = line.split()
+            rows[key] = [int(v) for v in vals]
+    return rows
+
+
+def _rand_volume(rng, T, H, W, lo=0.0, hi=1.0):
+    return rng.uniform(lo, hi, size=(T, H, W))
+
+
+# --------------------------------------------------------------------------- Eq. 9
+def test_combine_single_channel_passes_through():
+    """Alg. 1 initialisation note: one channel is assigned directly, without the sigmoid."""
+    rng = np.random.default_rng(0)
+    V = rng.uniform(size=(1, 3, 4, 5))
+    np.testing.assert_array_equal(oracle.combine(V, [2.0], 1.0), V[0])
+
+
+def test_combine_sigmoid_is_logistic():
+    """Eq. 9 with the standard logistic (reading of the printed 1/(1+e^x)): compare with
+    scipy's expit; a sign error in the exponent or a dropped bias fails."""
+    rng = np.random.default_rng(1)
+    V = rng.uniform(size=(3, 2, 4, 5))
+    w = np.array([0.7, -1.2, 2.5])
+    b = -0.3
+    z = np.tensordot(w, V, axes=1) + b
+    np.testing.assert_allclose(oracle.combine(V, w, b), scipy.special.expit(z), rtol=1e-15, atol=0)
+    assert np.all(oracle.combine(V, 10 * np.abs(w), 0.0) > 0.5)  # larger weights raise S_m
+
+
+# --------------------------------------------------------------------- paper counts
+def test_paper_tap_counts():
+    """Sec. 4.2: a 3x7x7 kernel means 147 neighbours per node (interior row of M), and 17 taps
+    in the separable filter form; the 10x20x20 video has 4000 nodes."""
+    g = _golden()
+    kt, kh, kw, dense, sep = g["kernel"]
+    r = ((kt - 1) // 2, (kh - 1) // 2, (kw - 1) // 2)
+    T, H, W = 5, 12, 12
+    f = np.full((T, H, W), 0.5)
+    M = oracle.affinity(f, f, 0.1, 1.0, r)
+    row = (2 * H + 6) * W + 6  # t=2, h=6, w=6: an interior node
+    assert M.indptr[row + 1] - M.indptr[row] == dense
+    assert sum(len(oracle.taps(ri, 1.0)) for ri in r) == sep
+    fr, hh, ww, nodes = g["graph"]
+    M2 = oracle.affinity(np.full((fr, hh, ww), 0.3), np.full((fr, hh, ww), 0.3), 0.1, 1.0, (1, 1, 1))
+    assert M2.shape == (nodes, nodes)
+    fr, hh, ww, approx = g["graph_approx"]
+    assert abs(fr * hh * ww - approx) / approx < 0.03
+
+
+# ------------------------------------------------------------------------- Eq. 2
+def test_affinity_symmetric_nonnegative():
+    """Sec. 3: M must be symmetric and non-negative (alpha <= 1, features in [0, 1])."""
+    rng = np.random.default_rng(2)
+    f = _rand_volume(rng, 3, 5, 7)
+    M = oracle.affinity(f, f, 0.2, 1.0, (1, 2, 2), sigma=(1.0, 1.3, 0.8))
+    D = M.toarray()
+    assert np.array_equal(D, D.T)        # bitwise symmetric
+    assert D.min() >= 0.0
+    np.testing.assert_allclose(np.diag(D), np.power(f.reshape(-1), 0.4), rtol=1e-15)  # u_i^2, G_ii = 1
+
+
+def test_two_node_closed_form():
+    """Eq. 2 on a 1x1x2 volume, worked by hand: with s = f = (0.2, 0.6), p = 0.5, alpha = 1 and
+    sigma_w = 1, M = [[0.2, b], [b, 0.6]] with b = sqrt(0.12) (1 - 0.16) e^{-1/2}; its top
+    eigenpair has the textbook 2x2 closed form."""
+    f = np.array([0.2, 0.6]).reshape(1, 1, 2)
+    M = oracle.affinity(f, f, 0.5, 1.0, (0, 0, 1), sigma=(1.0, 1.0, 1.0)).toarray()
+    b = np.sqrt(0.12) * 0.84 * np.exp(-0.5)
+    np.testing.assert_allclose(M, [[0.2, b], [b, 0.6]], rtol=1e-15, atol=1e-16)
+    lam = 0.4 + np.sqrt(0.2 ** 2 + b * b)
+    v = np.array([b, lam - 0.2])
+    v /= np.linalg.norm(v)
+    x, nu = oracle.power_csr(oracle.affinity(f, f, 0.5, 1.0, (0, 0, 1), sigma=(1.0, 1.0, 1.0)),
+                             np.ones(2), 200)
+    np.testing.assert_allclose(x, v, rtol=0, atol=1e-13)
+    np.testing.assert_allclose(nu[-1], lam, rtol=1e-13)
+
+
+def test_exact_kernel_approaches_taylor():
+    """Eq. 1 vs Eq. 2: the first-order expansion differs by O(alpha^2 d^4), so the angle between
+    the two principal eigenvectors shrinks like alpha^2 (Sec. 4.3 quantitative analysis)."""
+    rng = np.random.default_rng(3)
+    f = synth.drifting_blob(4, 10, 12, seed=7)[0].astype(np.float64)
+    angles = []
+    for alpha in (0.4, 0.2, 0.1):
+        Mt = oracle.affinity(f, f, 0.1, alpha, (1, 2, 2))
+        Me = oracle.affinity(f, f, 0.1, alpha, (1, 2, 2), exact=True)
+        xt = np.linalg.eigh(Mt.toarray())[1][:, -1]
+        xe = np.linalg.eigh(Me.toarray())[1][:, -1]
+        xe *= np.sign(xe @ xt)
+        angles.append(2 * np.arcsin(np.linalg.norm(xt - xe) / 2))
+    assert angles[0] > angles[1] > angles[2]
+    assert angles[1] / angles[2] > 3.0   # close to the factor 4 of a quadratic error
+
+
+# --------------------------------------------------------------------- Eq. 7 vs Eq. 2
+@pytest.mark.parametrize("shape,radius,sigma,alpha,p", [
+    ((3, 5, 7), (1, 2, 2), None, 1.0, 0.1),
+    ((4, 9, 6), (1, 3, 3), (0.9, 1.7, 2.1), 0.5, 0.2),
+    ((2, 3, 11), (2, 1, 4), (1.2, 0.6, 3.0), 2.0, 0.35),
+    ((5, 4, 4), (0, 0, 0), None, 1.0, 0.1),
+    ((1, 17, 3), (0, 7, 7), None, 1.0, 0.1),     # radius larger than the volume
+])
+def test_filter_form_equals_explicit_matrix(shape, radius, sigma, alpha, p):
+    """Eq. 6 -> Eq. 7 is an identity up to the factor alpha: A x = M x / alpha for any x.
+    Catches a dropped term, a wrong sign in Eq. 6, a transposed axis or wrong padding."""
+    rng = np.random.default_rng(sum(shape) + sum(radius))
+    s = _rand_volume(rng, *shape)
+    f = _rand_volume(rng, *shape)
+    s.reshape(-1)[::7] = 0.0                  # 0^p := 0 nodes
+    x = rng.uniform(-1, 1, size=shape)
+    M = oracle.affinity(s, f, p, alpha, radius, sigma=sigma)
+    y_mat = (M @ x.reshape(-1)) / alpha
+    y_fil = oracle.filter_apply(s, f, p, alpha, radius, x, sigma=sigma).reshape(-1)
+    scale = np.abs(M @ x.reshape(-1)).max()
+    assert np.abs(y_mat - y_fil).max() <= 1e-13 * scale
+
+
+def test_filter_form_symmetric_operator():
+    """<A y, z> = <y, A z> (M symmetric); boundary or index mistakes break this."""
+    rng = np.random.default_rng(4)
+    f = _rand_volume(rng, 4, 7, 9)
+    y = rng.normal(size=f.shape)
+    z = rng.normal(size=f.shape)
+    Ay = oracle.filter_apply(f, f, 0.1, 1.0, (1, 3, 2), y)
+    Az = oracle.filter_apply(f, f, 0.1, 1.0, (1, 3, 2), z)
+    assert abs(np.sum(Ay * z) - np.sum(y * Az)) <= 1e-12 * np.abs(Ay).sum()
+
+
+# ------------------------------------------------------------------- Eq. 3, 4, 8
+def test_power_iteration_matches_dense_eigensolver():
+    """Eq. 3: the limit of Eq. 4 + Eq. 8 is the principal eigenvector of M (Perron vector,
+    non-negative) and nu -> lambda_max.  Brute force with LAPACK on a 960-node volume."""
+    f = synth.drifting_blob(5, 12, 16, seed=11)[0].astype(np.float64)
+    M = oracle.affinity(f, f, 0.1, 1.0, (1, 2, 2))
+    evals, evecs = np.linalg.eigh(M.toarray())
+    v = evecs[:, -1] * np.sign(evecs[:, -1].sum())
+    ratio = evals[-2] / evals[-1]
+    K = int(np.ceil(np.log(1e-12) / np.log(ratio))) + 20
+    x, nu = oracle.power_csr(M, synth.uniform_start(M.shape[0]), K)
+    assert 2 * np.arcsin(np.linalg.norm(x - v) / 2) < 1e-8    # angle, well conditioned
+    np.testing.assert_allclose(nu[-1], evals[-1], rtol=1e-12)
+    assert x.min() >= 0.0
+    rho, res = oracle.rayleigh(lambda z: M @ z, x)
+    np.testing.assert_allclose(rho, evals[-1], rtol=1e-12)
+    assert res < 1e-9
+
+
+def test_kronecker_closed_form():
+    """Constant s = f: Eq. 2 reduces to M = u^2 G_t (x) G_h (x) G_w with each G_a the 1D
+    zero-padded Gaussian band matrix, so A = M/alpha has the top eigenpair
+    (u^2/alpha) l_t l_h l_w, v_t (x) v_h (x) v_w, each factor from a 1D dense eigensolver.
+    Every term of Eq. 7 matters here: 1/alpha - f^2 - f^2 + 2 f^2 = 1/alpha."""
+    T, H, W = 5, 9, 13
+    r = (1, 3, 2)
+    sig = (0.8, 1.6, 1.1)
+    fval, p, alpha = 0.7, 0.3, 0.8
+    f = np.full((T, H, W), fval)
+
+    def band(n, ra, sa):
+        d = np.arange(n)[:, None] - np.arange(n)[None, :]
+        return np.where(np.abs(d) <= ra, np.exp(-d * d / (2 * sa * sa)), 0.0)
+
+    vals, vecs = [], []
+    for n, ra, sa in zip((T, H, W), r, sig):
+        e, V = np.linalg.eigh(band(n, ra, sa))
+        vals.append(e[-1])
+        vecs.append(V[:, -1] * np.sign(V[:, -1].sum()))
+    u2 = fval ** (2 * p)
+    lam = u2 / alpha * vals[0] * vals[1] * vals[2]
+    v = np.einsum("a,b,c->abc", *vecs)
+    Av = oracle.filter_apply(f, f, p, alpha, r, v, sigma=sig)
+    np.testing.assert_allclose(Av, lam * v, rtol=0, atol=1e-13 * lam)
+    x, nu = oracle.power_filter(f, f, p, alpha, r, np.ones((T, H, W)), 400, sigma=sig)
+    np.testing.assert_allclose(x, v, atol=1e-10)
+    np.testing.assert_allclose(nu[-1], lam, rtol=1e-12)
+
+
+def test_diagonal_special_case():
+    """Radius (0, 0, 0): M = diag(u_i^2), so K steps from the uniform start give exactly
+    u^(2K) / ||u^(2K)|| (catches a wrong exponent p, e.g. s^(2p) for the unary term)."""
+    rng = np.random.default_rng(5)
+    f = _rand_volume(rng, 2, 3, 4, lo=0.2)
+    p, K = 0.35, 7
+    M = oracle.affinity(f, f, p, 1.0, (0, 0, 0))
+    x, nu = oracle.power_csr(M, np.ones(f.size), K)
+    ref = f.reshape(-1) ** (2 * p * K)
+    np.testing.assert_allclose(x, ref / np.linalg.norm(ref), rtol=1e-13)
+    xf, _ = oracle.power_filter(f, f, p, 1.0, (0, 0, 0), np.ones(f.shape), K)
+    np.testing.assert_allclose(xf.reshape(-1), ref / np.linalg.norm(ref), rtol=1e-13)
+
+
+def test_invariants_on_blob_volume():
+    """Perron-Frobenius and power-iteration invariants: x >= 0; nu_k non-decreasing
+    (log-convexity of ||A^k x|| for symmetric A); rho <= max row sum; zero-u slab decouples."""
+    V = synth.drifting_blob(6, 14, 15, seed=12)[0].astype(np.float64)
+    M = oracle.affinity(V, V, 0.1, 1.0, (1, 2, 2))
+    x, nu = oracle.power_csr(M, synth.uniform_start(V.size), 60)
+    assert x.min() >= 0.0
+    assert np.all(np.diff(nu) >= -1e-14 * nu[1:])
+    rho, _ = oracle.rayleigh(lambda z: M @ z, x)
+    assert rho <= np.abs(M).sum(axis=1).max() * (1 + 1e-14)
+    s = V.copy()
+    s[2:4] = 0.0                                   # two empty frames, r_t = 1
+    Ms = oracle.affinity(s, V, 0.1, 1.0, (1, 2, 2)).tocoo()
+    HW = 14 * 15
+    ti, tj = Ms.row // HW, Ms.col // HW
+    nz = Ms.data != 0
+    assert not np.any(((ti[nz] < 2) & (tj[nz] >= 4)) | ((ti[nz] >= 4) & (tj[nz] < 2)))
+
+
+# ---------------------------------------------------------------------- Sec. 3.4
+def _forward_loss(V, w, b, p, alpha, r, K, lossfn):
+    f = oracle.combine(V, w, b)
+    M = oracle.affinity(f, f, p, alpha, r)
+    x, _ = oracle.power_csr(M, synth.uniform_start(f.size), K)
+    return lossfn(x)
+
+
+@pytest.mark.parametrize("which", ["linear", "soft_iou"])
+def test_grad_matches_finite_differences(which):
+    """The reverse pass through K normalised steps equals central finite differences of the
+    forward pass (dL/dw_c and dL/db), C = 2."""
+    rng = np.random.default_rng(6)
+    V, m, _ = synth.multichannel(3, 6, 7, C=2, seed=21)
+    V = V.astype(np.float64)
+    w = np.array([1.3, -0.6])
+    b = 0.2
+    p, alpha, r, K = 0.2, 1.0, (1, 1, 2), 5
+    if which == "linear":
+        cvec = rng.normal(size=V[0].size)
+        lossfn = lambda x: float(cvec @ x)
+        gK = cvec
+        f = oracle.combine(V, w, b)
+        M = oracle.affinity(f, f, p, alpha, r)
+    else:
+        tgt = (m > 0.5).astype(np.float64).reshape(-1)
+        lossfn = lambda x: oracle.soft_iou_loss(x, tgt)[0]
+        f = oracle.combine(V, w, b)
+        M = oracle.affinity(f, f, p, alpha, r)
+        xK, _ = oracle.power_csr(M, synth.uniform_start(f.size), K)
+        gK = oracle.soft_iou_loss(xK, tgt)[1]
+    gw, gb = oracle.grad_csr(V, w, b, p, alpha, r, synth.uniform_start(V[0].size), K, gK)
+    h = 1e-6
+    for c in range(2):
+        wp, wm = w.copy(), w.copy()
+        wp[c] += h
+        wm[c] -= h
+        fd = (_forward_loss(V, wp, b, p, alpha, r, K, lossfn)
+              - _forward_loss(V, wm, b, p, alpha, r, K, lossfn)) / (2 * h)
+        assert abs(fd - gw[c]) <= 1e-6 * max(1.0, abs(fd)), (c, fd, gw[c])
+    fd = (_forward_loss(V, w, b + h, p, alpha, r, K, lossfn)
+          - _forward_loss(V, w, b - h, p, alpha, r, K, lossfn)) / (2 * h)
+    assert abs(fd - gb) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_soft_iou_loss_values_and_gradient():
+    """1 - soft-IoU: zero when the max-normalised x equals a binary target; 1 for disjoint
+    support; gradient equal to central differences."""
+    g = np.array([0.0, 1.0, 1.0, 0.0, 1.0])
+    assert oracle.soft_iou_loss(3.0 * g, g)[0] == pytest.approx(0.0, abs=1e-15)
+    assert oracle.soft_iou_loss(np.array([1.0, 0, 0, 1.0, 0]), g)[0] == pytest.approx(1.0)
+    rng = np.random.default_rng(7)
+    x = rng.uniform(0.1, 1.0, size=5)
+    _, dx = oracle.soft_iou_loss(x, g)
+    h = 1e-7
+    for i in range(5):
+        e = np.zeros(5)
+        e[i] = h
+        fd = (oracle.soft_iou_loss(x + e, g)[0] - oracle.soft_iou_loss(x - e, g)[0]) / (2 * h)
+        assert abs(fd - dx[i]) < 1e-7
+
+
+# ------------------------------------------------------------- warm-start network
+def test_conv3d_matches_scipy_correlate():
+    """The plain convolution loops equal scipy.ndimage.correlate (zero padding) summed over
+    input channels; catches a flipped kernel or a transposed tap index."""
+    rng = np.random.default_rng(8)
+    T, H, W, Cin, Cout = 3, 5, 6, 2, 3
+    x = rng.normal(size=(T, H, W, Cin))
+    wt = rng.normal(size=(Cout, 3, 3, 3, Cin))
+    b = rng.normal(size=Cout)
+    y = oracle.conv3d_fwd(x, wt, b)
+    for co in range(Cout):
+        ref = np.full((T, H, W), b[co])
+        for ci in range(Cin):
+            ref += scipy.ndimage.correlate(x[..., ci], wt[co, ..., ci], mode="constant", cval=0.0)
+        np.testing.assert_allclose(y[..., co], ref, rtol=1e-12, atol=1e-12)
+
+
+def test_conv3d_backward_matches_finite_differences():
+    rng = np.random.default_rng(9)
+    T, H, W, Cin, Cout = 2, 4, 3, 2, 2
+    x = rng.normal(size=(T, H, W, Cin))
+    wt = rng.normal(size=(Cout, 3, 3, 3, Cin))
+    b = rng.normal(size=Cout)
+    c = rng.normal(size=(T, H, W, Cout))
+    L = lambda xx, ww, bb: float(np.sum(c * oracle.conv3d_fwd(xx, ww, bb)))
+    dx, dw, db = oracle.conv3d_bwd(x, wt, c)
+    h = 1e-6
+    for idx in [(0, 1, 2, 1), (1, 3, 0, 0)]:
+        e = np.zeros_like(x)
+        e[idx] = h
+        assert abs((L(x + e, wt, b) - L(x - e, wt, b)) / (2 * h) - dx[idx]) < 1e-6
+    for idx in [(0, 1, 1, 1, 0), (1, 0, 2, 1, 1), (1, 2, 0, 0, 1)]:
+        e = np.zeros_like(wt)
+        e[idx] = h
+        assert abs((L(x, wt + e, b) - L(x, wt - e, b)) / (2 * h) - dw[idx]) < 1e-6
+    np.testing.assert_allclose(db, c.sum(axis=(0, 1, 2)), rtol=1e-12)
+
+
+def test_warmstart_network_gradient_matches_finite_differences():
+    rng = np.random.default_rng(10)
+    C, T, H, W = 3, 3, 4, 5
+    feats = rng.uniform(size=(C, T, H, W))
+    target = rng.uniform(size=(T, H, W))
+    dims = [C, 4, 4, 1]
+    params = [(rng.normal(scale=0.3, size=(dims[i + 1], 3, 3, 3, dims[i])),
+               rng.normal(scale=0.1, size=dims[i + 1])) for i in range(3)]
+    loss, grads = oracle.warmstart_backward(feats, params, target)
+    h = 1e-6
+    for li, idx in [(0, (1, 0, 1, 2, 2)), (1, (3, 2, 2, 0, 1)), (2, (0, 1, 1, 1, 3))]:
+        pp = [(w.copy(), b.copy()) for w, b in params]
+        pm = [(w.copy(), b.copy()) for w, b in params]
+        pp[li][0][idx] += h
+        pm[li][0][idx] -= h
+        fd = (oracle.warmstart_backward(feats, pp, target)[0]
+              - oracle.warmstart_backward(feats, pm, target)[0]) / (2 * h)
+        assert abs(fd - grads[li][0][idx]) < 1e-7 * max(1.0, abs(fd))

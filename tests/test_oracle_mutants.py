@@ -1,0 +1,78 @@
+"""Mutation check of the oracle's pins: plant a plausible mistake in a temporary copy of the
+oracle's C source, rebuild it, and require that the pin aimed at that mistake fails.
+
+Nothing is changed in ``oracle/``; each mutant lives in a pytest tmp directory.
+"""
+import ctypes
+import os
+import subprocess
+
+import pytest
+
+import oracle
+import tests.test_oracle as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "sfseg_oracle.c")
+
+# (name, text in the oracle, planted replacement, pins that must fail)
+MUTANTS = [
+    ("eq7_third_term_sign", "+ 2.0 * u[i] * f[i] * c3[i]", "- 2.0 * u[i] * f[i] * c3[i]",
+     ["test_kronecker_closed_form"]),
+    ("eq7_dropped_f2_term", "- u[i] * c2[i]", "- 0.0 * c2[i]",
+     ["test_kronecker_closed_form"]),
+    ("eq2_pair_sign", "(1.0 - alpha * df * df)", "(1.0 + alpha * df * df)",
+     ["test_two_node_closed_form"]),
+    ("filter_axes_swapped", "filter_axis(T, H, W, 2, rw, gw, in, out);",
+     "filter_axis(T, H, W, 2, rh, gh, in, out);", ["test_kronecker_closed_form"]),
+    ("unary_exponent", "return s > 0.0 ? pow(s, p) : 0.0;", "return s > 0.0 ? pow(s, 2.0 * p) : 0.0;",
+     ["test_diagonal_special_case"]),
+    ("sigmoid_sign", "f[i] = 1.0 / (1.0 + exp(-z));", "f[i] = 1.0 / (1.0 + exp(z));",
+     ["test_combine_sigmoid_is_logistic"]),
+    ("gradient_pair_sign", "- 2.0 * alpha * ua * ub * d;", "+ 2.0 * alpha * ua * ub * d;",
+     ["test_grad_matches_finite_differences"]),
+    ("wrap_padding", "if (tt < 0 || tt >= T || hh < 0 || hh >= H || ww < 0 || ww >= W) continue;",
+     "tt = (tt + T) % T; hh = (hh + H) % H; ww = (ww + W) % W;",
+     ["test_filter_form_equals_explicit_matrix"]),
+    ("l1_renormalisation",
+     "orc_spmv(N, rowptr, col, val, x_out, y);\n        double nu = sqrt(orc_sumsq(y, N));",
+     "orc_spmv(N, rowptr, col, val, x_out, y);\n        double nu = 0.0;\n"
+     "        for (int64_t q = 0; q < N; ++q) nu += fabs(y[q]);",
+     ["test_two_node_closed_form", "test_power_iteration_matches_dense_eigensolver"]),
+]
+
+
+def _build_mutant(tmp_path, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor not unique: {old!r}"
+    path = tmp_path / "mutant.c"
+    path.write_text(src.replace(old, new))
+    so = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                           str(path), "-o", str(so), "-lm"])
+    lib = ctypes.CDLL(str(so))
+    for name, rt in [("orc_build_affinity", ctypes.c_int64), ("orc_sumsq", ctypes.c_double),
+                     ("orc_dot", ctypes.c_double), ("orc_power_csr", ctypes.c_int),
+                     ("orc_power_filter", ctypes.c_int), ("orc_grad_csr", ctypes.c_int),
+                     ("orc_num_threads", ctypes.c_int)]:
+        getattr(lib, name).restype = rt
+    return lib
+
+
+def _run_pin(name):
+    fn = getattr(pins, name)
+    if name == "test_grad_matches_finite_differences":
+        fn("linear")
+    elif name == "test_filter_form_equals_explicit_matrix":
+        fn((3, 5, 7), (1, 2, 2), None, 1.0, 0.1)
+    else:
+        fn()
+
+
+@pytest.mark.parametrize("name,old,new,targets", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pin_catches_planted_mistake(tmp_path, monkeypatch, name, old, new, targets):
+    lib = _build_mutant(tmp_path, old, new)
+    oracle._load()                      # make sure the real library is loaded first
+    monkeypatch.setattr(oracle, "_lib", lib)
+    for t in targets:
+        with pytest.raises((AssertionError, FloatingPointError)):
+            _run_pin(t)
