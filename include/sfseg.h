@@ -1,0 +1,163 @@
+/*
+ * sfseg.h -- C ABI of the GB300 (sm_103a) SFSeg / SFSeg++ power-iteration library.
+ *
+ * Method: Burceanu & Leordeanu, "SFSeg / SFSeg++" (arXiv 2212.08058).  The library computes
+ * the principal eigenvector of the pixel-level space-time affinity matrix M of Eq. 2,
+ *     M_ij = u_i u_j [1 - alpha (f_i - f_j)^2] G_ij,   u = s^p,  (0^p := 0)
+ * without forming M, by power iteration (Eq. 4, Eq. 8) in the three-filter form of Eq. 7 / Eq. 10:
+ *     A x = u (1/alpha - f^2) G*(u x) - u G*(f^2 u x) + 2 u f G*(f u x),      A = M / alpha,
+ *     x_{k+1} = A x_k / ||A x_k||_2.
+ * Features are combined first with Eq. 9 (SFSeg++): s = f = sigmoid(sum_c w_c V_c + b); with a
+ * single channel s = f = V_0 (Alg. 1, initialisation note).  G is the unnormalised Gaussian
+ * exp(-0.5 (dt^2/st^2 + dh^2/sh^2 + dw^2/sw^2)) truncated to the box |dt|<=rt, |dh|<=rh,
+ * |dw|<=rw, with zero padding at the volume border (Sec. 4.2: separable, three 1D passes).
+ *
+ * Conventions for every call
+ *   - Volumes are row-major [T][H][W] (w fastest); feature tensors are [C][T][H][W].
+ *   - "device" pointers are CUDA global-memory pointers owned by the caller; the library never
+ *     frees or keeps them beyond the call.  "host" pointers are ordinary CPU memory.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are asynchronous on it
+ *     unless they return host scalars, which they document as synchronising.
+ *   - Every call returns an sfseg_status; on failure sfseg_last_error() gives a message
+ *     (thread-local, valid until the next call on the same thread).  No exception crosses the ABI.
+ *   - A handle is not thread-safe and its calls must not overlap on different streams.
+ */
+#ifndef SFSEG_H
+#define SFSEG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum sfseg_status {
+    SFSEG_OK = 0,
+    SFSEG_ERR_INVALID_ARG = 1, /* null pointer, parameter out of range */
+    SFSEG_ERR_SHAPE = 2,       /* empty volume, radius beyond the supported maximum, size mismatch */
+    SFSEG_ERR_DTYPE = 3,       /* unknown dtype code */
+    SFSEG_ERR_CUDA = 4,        /* a CUDA runtime call failed (message holds the CUDA error) */
+    SFSEG_ERR_OOM = 5,         /* device allocation failed */
+    SFSEG_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+    SFSEG_ERR_NONFINITE = 7,   /* a feature is negative, NaN or Inf, or a norm became non-finite */
+    SFSEG_ERR_ZERO_NORM = 8,   /* an iterate became exactly zero (e.g. u = 0 everywhere) */
+    SFSEG_ERR_STATE = 9,       /* call order violated (no features set, no recorded forward, ...) */
+    SFSEG_ERR_UNSUPPORTED = 10 /* valid request this build does not implement */
+} sfseg_status;
+
+typedef enum sfseg_dtype {
+    SFSEG_F32 = 0,  /* IEEE float32 */
+    SFSEG_BF16 = 1  /* bfloat16 (1-8-7), round to nearest even when the library writes it */
+} sfseg_dtype;
+
+typedef enum sfseg_init {
+    SFSEG_INIT_USER = 0,    /* start from the caller's x (any non-negative, non-zero vector) */
+    SFSEG_INIT_UNIFORM = 1, /* x_0 = 1/sqrt(N) (Sec. 4: "a uniform vector") */
+    SFSEG_INIT_SMAP = 2     /* x_0 = S_m / ||S_m|| (Alg. 1: X_m <- S_m) */
+} sfseg_init;
+
+/* Method hyper-parameters (Eq. 2): alpha > 0 weights the pairwise term, p > 0 the unary term.
+ * The paper uses alpha = 1, p = 0.1 (unsupervised) or 0.2 (semi-supervised) (Sec. 5.1.1). */
+typedef struct sfseg_params {
+    double alpha;
+    double p;
+} sfseg_params;
+
+/* Space-time neighbourhood (Eq. 1 distance term; Sec. 4.2 separable 3D Gaussian).
+ * 0 <= rt <= 4, 0 <= rh, rw <= 8; sigma_* > 0 wherever the matching radius is > 0. */
+typedef struct sfseg_neighborhood {
+    int rt, rh, rw;
+    float sigma_t, sigma_h, sigma_w;
+} sfseg_neighborhood;
+
+typedef struct sfseg_handle sfseg_handle;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int sfseg_version(void);
+
+/* Message of the last failed call on this thread ("" if none).  Never NULL. */
+const char* sfseg_last_error(void);
+
+/* Create a handle for C-channel feature volumes of T x H x W voxels and allocate its device
+ * workspace (combined features, two iterate buffers, FP64 accumulators): about 12 N bytes plus
+ * 2 N more once bf16 storage is used, N = T*H*W.  `out` receives the handle (host pointer).
+ * Errors: INVALID_ARG (null, alpha <= 0, p <= 0, C < 1 or C > 64), SHAPE (T, H or W < 1,
+ * N >= 2^31), OOM, CUDA. */
+int sfseg_create(const sfseg_params* prm, int C, int T, int H, int W, sfseg_handle** out);
+
+/* Free the handle and its workspace (synchronises the device).  NULL is a no-op. */
+int sfseg_destroy(sfseg_handle* h);
+
+/* Eq. 9 / Alg. 1 lines 1-2: combine the C channels of `features` (device, [C][T][H][W],
+ * `dtype`) into f = s inside the handle.  `weights` (host, C floats) and `bias` are ignored when
+ * C == 1.  Features must be finite and >= 0 (checked on the device; reported by the next
+ * synchronising call as NONFINITE).  Asynchronous. */
+int sfseg_set_features(sfseg_handle* h, const void* features, int dtype, const float* weights,
+                       float bias, void* stream);
+
+/* Eq. 7 + Eq. 8 (Alg. 1 main loop, continuous iterations): `iters` >= 0 power iterations.
+ *   features      device [C][T][H][W] in `dtype`, or NULL to reuse the features already set.
+ *   weights/bias  as for sfseg_set_features (used only when features != NULL).
+ *   nb            neighbourhood (host struct).
+ *   iters_bf16    the first min(iters_bf16, iters) iterations keep the iterate and f in bf16
+ *                 (FP32 arithmetic); the remaining ones run with FP32 storage.
+ *   x_inout       device [T][H][W] float32.  Read as the start vector when init ==
+ *                 SFSEG_INIT_USER; always overwritten with the unit-norm x_iters.
+ *   init          sfseg_init.
+ *   record_every  > 0 keeps checkpoints every `record_every` iterations for sfseg_backward
+ *                 (about N*4*(iters/record_every + 1) bytes); 0 records nothing.
+ *   norms_out     host array of `iters` doubles or NULL.  When given, the call synchronises and
+ *                 writes nu_k = ||A x_{k-1}||_2 (k = 1..iters), which converges to lambda_max(A);
+ *                 it then also reports ZERO_NORM / NONFINITE found on the device.
+ * Errors: INVALID_ARG, SHAPE (radius limits), STATE (no features), OOM, CUDA, and with
+ * norms_out ZERO_NORM / NONFINITE. */
+int sfseg_power_iterate(sfseg_handle* h, const void* features, int dtype, const float* weights,
+                        float bias, const sfseg_neighborhood* nb, int iters, int iters_bf16,
+                        float* x_inout, int init, int record_every, double* norms_out,
+                        void* stream);
+
+/* One application y = A x of the Eq. 7 operator (FP32 features and storage).
+ * x, y: device [T][H][W] float32 (may not alias).  Asynchronous. */
+int sfseg_apply(sfseg_handle* h, const sfseg_neighborhood* nb, const float* x, float* y,
+                void* stream);
+
+/* Eq. 3: Rayleigh quotient rho = x'Ax / x'x and eigen-residual ||Ax - rho x|| / (rho ||x||)
+ * of the FP32 operator (FP64 reductions).  x: device [T][H][W] float32.  rho, residual: host
+ * doubles (either may be NULL).  Synchronises the stream.  Uses the handle's iterate buffer as
+ * scratch. */
+int sfseg_rayleigh(sfseg_handle* h, const sfseg_neighborhood* nb, const float* x, double* rho,
+                   double* residual, void* stream);
+
+/* Sec. 3.4 (learning the Eq. 9 weights through the unrolled iteration): given
+ * grad_x = dL/dx_K (device [T][H][W] float32) for the x_K of the last sfseg_power_iterate call
+ * on this handle (which must have used record_every > 0, C > 1, and features != NULL or set),
+ * write dL/dw (host, C floats) and dL/db (host, 1 float).  The adjoint runs backwards through
+ * the K normalised steps, recomputing iterates between checkpoints.  Synchronises.
+ * Errors: STATE (no recorded forward), UNSUPPORTED (C == 1, or bf16 iterations recorded). */
+int sfseg_backward(sfseg_handle* h, const sfseg_neighborhood* nb, const float* grad_x,
+                   float* grad_weights, float* grad_bias, void* stream);
+
+/* Learning loss: L = 1 - soft-IoU(xh, g), xh = x / max(x), soft-IoU = sum(xh g) /
+ * sum(xh + g - xh g), and dL/dx (the max differentiated at its first argmax).
+ * x, target: device [T][H][W] float32 of this handle's size; grad_x: device float32 or NULL;
+ * loss: host double.  Synchronises. */
+int sfseg_soft_iou_loss(sfseg_handle* h, const float* x, const float* target, double* loss,
+                        float* grad_x, void* stream);
+
+/* Instrumentation (no counterpart in the paper).  When enabled, each sfseg_power_iterate call
+ * records two CUDA events on its stream, before its first and after its last iteration-kernel
+ * launch.  sfseg_iter_timing waits for the recorded events, returns the summed milliseconds and
+ * the number of iteration launches they bracket (host outputs), and resets both.  Disabled by
+ * default; enabling it adds two event records per call. */
+int sfseg_enable_iter_timing(sfseg_handle* h, int on);
+int sfseg_iter_timing(sfseg_handle* h, double* ms, int64_t* launches);
+
+/* Number of CUDA kernels this library has launched in the process so far (host output). */
+int sfseg_kernel_launches(int64_t* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SFSEG_H */

@@ -174,21 +174,24 @@ int orc_power_csr(int64_t N, const int64_t* rowptr, const int64_t* col, const do
     return 0;
 }
 
-/* One 1D zero-padded correlation along an axis of a T x H x W volume (in place via tmp).
- * axis 0 = t, 1 = h, 2 = w.  The Gaussian factor is even, so correlation == convolution. */
+/* One 1D zero-padded correlation along an axis of a T x H x W volume.
+ * axis 0 = t, 1 = h, 2 = w.  The Gaussian factor is even, so correlation == convolution.
+ * Taps that fall outside the volume are skipped (zero padding); the valid tap range of each
+ * output is computed once, and the taps are summed in increasing offset order. */
 static void filter_axis(int T, int H, int W, int axis, int r, const double* g, const double* in, double* out) {
     int64_t HW = (int64_t)H * W;
+    int64_t step = axis == 0 ? HW : (axis == 1 ? W : 1);
+    int n = axis == 0 ? T : (axis == 1 ? H : W);
 #pragma omp parallel for collapse(2) schedule(static)
     for (int t = 0; t < T; ++t) {
         for (int h = 0; h < H; ++h) {
             for (int w = 0; w < W; ++w) {
+                int pos = axis == 0 ? t : (axis == 1 ? h : w);
+                int lo = pos - r < 0 ? -pos : -r;
+                int hi = pos + r > n - 1 ? n - 1 - pos : r;
+                const double* src = in + (int64_t)t * HW + (int64_t)h * W + w;
                 double acc = 0.0;
-                for (int d = -r; d <= r; ++d) {
-                    int tt = t, hh = h, ww = w;
-                    if (axis == 0) tt += d; else if (axis == 1) hh += d; else ww += d;
-                    if (tt < 0 || tt >= T || hh < 0 || hh >= H || ww < 0 || ww >= W) continue;
-                    acc += g[d + r] * in[(int64_t)tt * HW + (int64_t)hh * W + ww];
-                }
+                for (int d = lo; d <= hi; ++d) acc += g[d + r] * src[d * step];
                 out[(int64_t)t * HW + (int64_t)h * W + w] = acc;
             }
         }

@@ -1,0 +1,481 @@
+// api.cu -- the C ABI of libsfseg.so (declared in include/sfseg.h): argument checking, the
+// handle's device workspace, and the sequence of kernel launches of each call.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sfseg.h"
+#include "common.cuh"
+#include "launch.h"
+
+using namespace sfseg;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+#define SFSEG_CUDA(call)                                                                     \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(e_ == cudaErrorMemoryAllocation ? SFSEG_ERR_OOM : SFSEG_ERR_CUDA,    \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+    } while (0)
+
+#define SFSEG_LAUNCHED()                                                                     \
+    do {                                                                                     \
+        cudaError_t e_ = cudaGetLastError();                                                 \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(SFSEG_ERR_CUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t n) {
+    return cudaMalloc((void**)p, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+}
+
+}  // namespace
+
+struct sfseg_handle {
+    int C = 0;
+    double alpha = 1.0, p = 0.1;
+    Geom g{};
+    int64_t N = 0, NP = 0;            // voxels; elements of an internal (pitched) volume
+    float* f32 = nullptr;             // combined features, float32
+    __nv_bfloat16* fbf = nullptr;     // bf16 copy (allocated on first bf16 use)
+    bool fbf_valid = false;
+    bool features_set = false;
+    const void* feat_ptr = nullptr;   // caller's last feature tensor (for the weight gradient)
+    int feat_dtype = 0;
+    void* vbuf[2] = {nullptr, nullptr};   // iterate ping-pong, NP floats each
+    double* acc = nullptr;            // per-step squared norms
+    int acc_cap = 0;
+    double* scratch = nullptr;        // 64 doubles for reductions
+    unsigned long long* amax = nullptr;
+    int* flags = nullptr;
+    float* wdev = nullptr;            // channel weights on the device
+    // recorded forward (for the adjoint)
+    int rec_K = 0, rec_every = 0;
+    bool rec_valid = false;
+    std::vector<float*> ckpt;         // x~ at k = 0, every, 2 every, ... and at K (last entry)
+    double* rec_acc = nullptr;
+    int rec_acc_cap = 0;
+    // adjoint workspace
+    float* gbuf[2] = {nullptr, nullptr};
+    float* gz = nullptr;
+    std::vector<float*> seg;
+    double* dots = nullptr;
+    int dots_cap = 0;
+    // optional CUDA-event timing of the iteration kernels
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_free;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
+    int64_t timed_launches = 0;
+};
+
+static cudaEvent_t take_event(sfseg_handle* h) {
+    if (!h->ev_free.empty()) {
+        cudaEvent_t e = h->ev_free.back();
+        h->ev_free.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+static int check_handle(sfseg_handle* h) {
+    if (!h) return fail(SFSEG_ERR_INVALID_ARG, "null handle");
+    return SFSEG_OK;
+}
+
+static int make_taps(const sfseg_neighborhood* nb, Taps* tp) {
+    if (!nb) return fail(SFSEG_ERR_INVALID_ARG, "null neighborhood");
+    if (nb->rt < 0 || nb->rh < 0 || nb->rw < 0 || nb->rt > kMaxRT || nb->rh > kMaxRH || nb->rw > kMaxRW)
+        return fail(SFSEG_ERR_SHAPE, "radius out of range (0 <= rt <= 4, 0 <= rh, rw <= 8)");
+    const float sg[3] = {nb->sigma_t, nb->sigma_h, nb->sigma_w};
+    const int rr[3] = {nb->rt, nb->rh, nb->rw};
+    for (int a = 0; a < 3; ++a)
+        if (rr[a] > 0 && !(sg[a] > 0.f && std::isfinite(sg[a])))
+            return fail(SFSEG_ERR_INVALID_ARG, "sigma must be finite and > 0 where the radius is > 0");
+    std::memset(tp, 0, sizeof(Taps));
+    tp->rt = nb->rt;
+    tp->rh = nb->rh;
+    tp->rw = nb->rw;
+    float* dst[3] = {tp->gt, tp->gh, tp->gw};
+    for (int a = 0; a < 3; ++a)
+        for (int d = -rr[a]; d <= rr[a]; ++d)
+            dst[a][d + rr[a]] = rr[a] == 0 ? 1.f : (float)std::exp(-(double)d * d / (2.0 * (double)sg[a] * sg[a]));
+    return SFSEG_OK;
+}
+
+static int ensure_acc(double** buf, int* cap, int need) {
+    if (*cap >= need) return SFSEG_OK;
+    if (*buf) cudaFree(*buf);
+    *buf = nullptr;
+    *cap = 0;
+    int n = need < 1024 ? 1024 : need;
+    SFSEG_CUDA(dalloc(buf, (size_t)n));
+    *cap = n;
+    return SFSEG_OK;
+}
+
+static int read_flags(sfseg_handle* h, cudaStream_t s) {
+    int fl = 0;
+    SFSEG_CUDA(cudaMemcpyAsync(&fl, h->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    SFSEG_CUDA(cudaStreamSynchronize(s));
+    if (fl) SFSEG_CUDA(cudaMemsetAsync(h->flags, 0, sizeof(int), s));
+    if (fl & kFlagBadFeature) return fail(SFSEG_ERR_NONFINITE, "features must be finite and >= 0");
+    if (fl & kFlagNonfinite) return fail(SFSEG_ERR_NONFINITE, "an iterate norm became NaN or Inf");
+    if (fl & kFlagZeroNorm) return fail(SFSEG_ERR_ZERO_NORM, "an iterate became zero (u = 0 on its support?)");
+    return SFSEG_OK;
+}
+
+extern "C" {
+
+int sfseg_version(void) { return 100; }
+
+const char* sfseg_last_error(void) { return g_err.c_str(); }
+
+int sfseg_create(const sfseg_params* prm, int C, int T, int H, int W, sfseg_handle** out) {
+    if (!prm || !out) return fail(SFSEG_ERR_INVALID_ARG, "null argument");
+    *out = nullptr;
+    if (!(prm->alpha > 0.0) || !std::isfinite(prm->alpha)) return fail(SFSEG_ERR_INVALID_ARG, "alpha must be > 0");
+    if (!(prm->p > 0.0) || !std::isfinite(prm->p)) return fail(SFSEG_ERR_INVALID_ARG, "p must be > 0");
+    if (C < 1 || C > 64) return fail(SFSEG_ERR_INVALID_ARG, "C must be in [1, 64]");
+    if (T < 1 || H < 1 || W < 1) return fail(SFSEG_ERR_SHAPE, "empty volume");
+    const int64_t N = (int64_t)T * H * W;
+    if (N >= (int64_t(1) << 31)) return fail(SFSEG_ERR_SHAPE, "volume must have fewer than 2^31 voxels");
+    sfseg_handle* h = new sfseg_handle();
+    h->C = C;
+    h->alpha = prm->alpha;
+    h->p = prm->p;
+    h->g.T = T;
+    h->g.H = H;
+    h->g.W = W;
+    h->g.pitch = (W + 31) / 32 * 32;
+    h->N = N;
+    h->NP = (int64_t)T * H * h->g.pitch;
+    int rc = SFSEG_OK;
+    auto chk = [&](cudaError_t e) {
+        if (e != cudaSuccess && rc == SFSEG_OK)
+            rc = fail(e == cudaErrorMemoryAllocation ? SFSEG_ERR_OOM : SFSEG_ERR_CUDA,
+                      std::string("sfseg_create: ") + cudaGetErrorString(e));
+    };
+    chk(dalloc(&h->f32, (size_t)h->NP));
+    chk(dalloc((float**)&h->vbuf[0], (size_t)h->NP));
+    chk(dalloc((float**)&h->vbuf[1], (size_t)h->NP));
+    chk(dalloc(&h->scratch, 64));
+    chk(dalloc(&h->amax, 1));
+    chk(dalloc(&h->flags, 1));
+    chk(dalloc(&h->wdev, 64));
+    if (rc == SFSEG_OK) chk(cudaMemset(h->flags, 0, sizeof(int)));
+    if (rc == SFSEG_OK) chk(cudaMemset(h->f32, 0, (size_t)h->NP * sizeof(float)));
+    if (rc == SFSEG_OK) rc = ensure_acc(&h->acc, &h->acc_cap, 1024);
+    if (rc != SFSEG_OK) {
+        sfseg_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return SFSEG_OK;
+}
+
+int sfseg_destroy(sfseg_handle* h) {
+    if (!h) return SFSEG_OK;
+    cudaDeviceSynchronize();
+    cudaFree(h->f32);
+    cudaFree(h->fbf);
+    cudaFree(h->vbuf[0]);
+    cudaFree(h->vbuf[1]);
+    cudaFree(h->acc);
+    cudaFree(h->scratch);
+    cudaFree(h->amax);
+    cudaFree(h->flags);
+    cudaFree(h->wdev);
+    for (float* p : h->ckpt) cudaFree(p);
+    cudaFree(h->rec_acc);
+    cudaFree(h->gbuf[0]);
+    cudaFree(h->gbuf[1]);
+    cudaFree(h->gz);
+    for (float* p : h->seg) cudaFree(p);
+    cudaFree(h->dots);
+    for (cudaEvent_t e : h->ev_free) cudaEventDestroy(e);
+    for (auto& pr : h->ev_pending) {
+        cudaEventDestroy(pr.first);
+        cudaEventDestroy(pr.second);
+    }
+    delete h;
+    return SFSEG_OK;
+}
+
+int sfseg_set_features(sfseg_handle* h, const void* features, int dtype, const float* weights, float bias,
+                       void* stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (!features) return fail(SFSEG_ERR_INVALID_ARG, "null features");
+    if (dtype != SFSEG_F32 && dtype != SFSEG_BF16) return fail(SFSEG_ERR_DTYPE, "dtype must be F32 or BF16");
+    if (h->C > 1 && !weights) return fail(SFSEG_ERR_INVALID_ARG, "C > 1 needs channel weights");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (h->C > 1) {
+        for (int c = 0; c < h->C; ++c)
+            if (!std::isfinite(weights[c])) return fail(SFSEG_ERR_INVALID_ARG, "non-finite channel weight");
+        SFSEG_CUDA(cudaMemcpyAsync(h->wdev, weights, sizeof(float) * h->C, cudaMemcpyHostToDevice, s));
+    }
+    launch_combine(features, dtype, h->C, h->g, h->wdev, bias, h->f32, h->fbf, h->flags, s);
+    SFSEG_LAUNCHED();
+    h->fbf_valid = h->fbf != nullptr;
+    h->features_set = true;
+    h->feat_ptr = features;
+    h->feat_dtype = dtype;
+    h->rec_valid = false;
+    return SFSEG_OK;
+}
+
+int sfseg_power_iterate(sfseg_handle* h, const void* features, int dtype, const float* weights, float bias,
+                        const sfseg_neighborhood* nb, int iters, int iters_bf16, float* x_inout, int init,
+                        int record_every, double* norms_out, void* stream) {
+    if (int rc = check_handle(h)) return rc;
+    Taps tp;
+    if (int rc = make_taps(nb, &tp)) return rc;
+    if (iters < 0 || iters > (1 << 20)) return fail(SFSEG_ERR_INVALID_ARG, "iters must be in [0, 2^20]");
+    if (!x_inout) return fail(SFSEG_ERR_INVALID_ARG, "null x_inout");
+    if (init < SFSEG_INIT_USER || init > SFSEG_INIT_SMAP) return fail(SFSEG_ERR_INVALID_ARG, "bad init");
+    if (record_every < 0) return fail(SFSEG_ERR_INVALID_ARG, "record_every must be >= 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int bf = iters_bf16 < 0 ? 0 : (iters_bf16 > iters ? iters : iters_bf16);
+    if (record_every > 0 && bf > 0)
+        return fail(SFSEG_ERR_UNSUPPORTED, "recording for the adjoint needs float32 iterations");
+    if (bf > 0 && !h->fbf) {
+        SFSEG_CUDA(dalloc(&h->fbf, (size_t)h->NP));
+        SFSEG_CUDA(cudaMemsetAsync(h->fbf, 0, (size_t)h->NP * sizeof(__nv_bfloat16), s));
+        h->fbf_valid = false;
+    }
+    if (features) {
+        if (int rc = sfseg_set_features(h, features, dtype, weights, bias, stream)) return rc;
+    } else if (!h->features_set) {
+        return fail(SFSEG_ERR_STATE, "no features: pass them or call sfseg_set_features first");
+    }
+    if (bf > 0 && !h->fbf_valid) {
+        launch_to_bf16(h->f32, h->fbf, h->NP, s);
+        SFSEG_LAUNCHED();
+        h->fbf_valid = true;
+    }
+    const bool record = record_every > 0;
+    double* acc = nullptr;
+    if (record) {
+        if (int rc = ensure_acc(&h->rec_acc, &h->rec_acc_cap, iters + 2)) return rc;
+        acc = h->rec_acc;
+        const int need = (iters > 0 ? (iters - 1) / record_every + 1 : 1) + 1;
+        while ((int)h->ckpt.size() < need) {
+            float* p = nullptr;
+            SFSEG_CUDA(dalloc(&p, (size_t)h->NP));
+            h->ckpt.push_back(p);
+        }
+        h->rec_valid = false;
+    } else {
+        if (int rc = ensure_acc(&h->acc, &h->acc_cap, iters + 2)) return rc;
+        acc = h->acc;
+    }
+    SFSEG_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (iters + 1), s));
+    const float inv_alpha = (float)(1.0 / h->alpha), p = (float)h->p;
+    const int vt0 = bf > 0 ? kBF16 : kF32;
+    float* last_ckpt = record ? h->ckpt.back() : nullptr;
+    launch_prologue(init, x_inout, h->f32, p, h->g, h->vbuf[0], vt0, record ? h->ckpt[0] : nullptr,
+                    iters == 0 ? x_inout : nullptr, acc, s);
+    SFSEG_LAUNCHED();
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    if (h->timing && iters > 0) {
+        ev0 = take_event(h);
+        ev1 = take_event(h);
+        SFSEG_CUDA(cudaEventRecord(ev0, s));
+    }
+    for (int k = 0; k < iters; ++k) {
+        const bool last = k == iters - 1;
+        const int vin_t = k < bf ? kBF16 : kF32;
+        const int out_t = (k + 1 < bf) ? kBF16 : kF32;
+        const void* fptr = k < bf ? (const void*)h->fbf : (const void*)h->f32;
+        float* ck = nullptr;
+        if (record) {
+            if (last) ck = last_ckpt;
+            else if ((k + 1) % record_every == 0) ck = h->ckpt[(k + 1) / record_every];
+        }
+        launch_iterate(h->vbuf[k & 1], vin_t, last ? (void*)x_inout : h->vbuf[(k + 1) & 1], out_t, last, fptr,
+                       vin_t, ck, h->g, tp, inv_alpha, p, acc + k, acc + k + 1, h->flags, s);
+        SFSEG_LAUNCHED();
+    }
+    if (ev1) {
+        SFSEG_CUDA(cudaEventRecord(ev1, s));
+        h->ev_pending.emplace_back(ev0, ev1);
+        h->timed_launches += iters;
+    }
+    launch_scale_inv_norm(x_inout, h->N, acc + iters, h->flags, s);
+    SFSEG_LAUNCHED();
+    if (record) {
+        h->rec_K = iters;
+        h->rec_every = record_every;
+        h->rec_valid = iters > 0;
+    }
+    if (norms_out) {
+        std::vector<double> a((size_t)iters + 1);
+        SFSEG_CUDA(cudaMemcpyAsync(a.data(), acc, sizeof(double) * (iters + 1), cudaMemcpyDeviceToHost, s));
+        if (int rc = read_flags(h, s)) return rc;
+        for (int k = 0; k < iters; ++k) norms_out[k] = std::sqrt(a[k + 1]);
+    }
+    return SFSEG_OK;
+}
+
+int sfseg_enable_iter_timing(sfseg_handle* h, int on) {
+    if (int rc = check_handle(h)) return rc;
+    h->timing = on != 0;
+    return SFSEG_OK;
+}
+
+int sfseg_iter_timing(sfseg_handle* h, double* ms, int64_t* launches) {
+    if (int rc = check_handle(h)) return rc;
+    if (!ms || !launches) return fail(SFSEG_ERR_INVALID_ARG, "null argument");
+    double total = 0.0;
+    for (auto& pr : h->ev_pending) {
+        SFSEG_CUDA(cudaEventSynchronize(pr.second));
+        float t = 0.f;
+        SFSEG_CUDA(cudaEventElapsedTime(&t, pr.first, pr.second));
+        total += t;
+        h->ev_free.push_back(pr.first);
+        h->ev_free.push_back(pr.second);
+    }
+    h->ev_pending.clear();
+    *ms = total;
+    *launches = h->timed_launches;
+    h->timed_launches = 0;
+    return SFSEG_OK;
+}
+
+int sfseg_kernel_launches(int64_t* count) {
+    if (!count) return fail(SFSEG_ERR_INVALID_ARG, "null argument");
+    *count = launches_so_far();
+    return SFSEG_OK;
+}
+
+int sfseg_apply(sfseg_handle* h, const sfseg_neighborhood* nb, const float* x, float* y, void* stream) {
+    if (int rc = check_handle(h)) return rc;
+    Taps tp;
+    if (int rc = make_taps(nb, &tp)) return rc;
+    if (!x || !y) return fail(SFSEG_ERR_INVALID_ARG, "null x or y");
+    if (x == y) return fail(SFSEG_ERR_INVALID_ARG, "x and y must not alias");
+    if (!h->features_set) return fail(SFSEG_ERR_STATE, "no features set");
+    launch_apply(x, h->g.W, y, h->g.W, h->f32, h->g, tp, (float)(1.0 / h->alpha), (float)h->p, nullptr, nullptr,
+                 h->flags, (cudaStream_t)stream);
+    SFSEG_LAUNCHED();
+    return SFSEG_OK;
+}
+
+int sfseg_rayleigh(sfseg_handle* h, const sfseg_neighborhood* nb, const float* x, double* rho, double* residual,
+                   void* stream) {
+    if (int rc = check_handle(h)) return rc;
+    Taps tp;
+    if (int rc = make_taps(nb, &tp)) return rc;
+    if (!x) return fail(SFSEG_ERR_INVALID_ARG, "null x");
+    if (!h->features_set) return fail(SFSEG_ERR_STATE, "no features set");
+    cudaStream_t s = (cudaStream_t)stream;
+    float* y = (float*)h->vbuf[0];
+    double* a = h->scratch;
+    SFSEG_CUDA(cudaMemsetAsync(a, 0, sizeof(double) * 4, s));
+    launch_apply(x, h->g.W, y, h->g.W, h->f32, h->g, tp, (float)(1.0 / h->alpha), (float)h->p, nullptr, nullptr,
+                 h->flags, s);
+    launch_dot2(x, y, h->N, a, s);
+    launch_resid(x, y, h->N, a, s);
+    SFSEG_LAUNCHED();
+    double hv[3];
+    SFSEG_CUDA(cudaMemcpyAsync(hv, a, sizeof(hv), cudaMemcpyDeviceToHost, s));
+    if (int rc = read_flags(h, s)) return rc;
+    if (!(hv[1] > 0.0)) return fail(SFSEG_ERR_ZERO_NORM, "x is zero");
+    const double r = hv[0] / hv[1];
+    if (rho) *rho = r;
+    if (residual) *residual = std::sqrt(hv[2] / hv[1]) / r;
+    return SFSEG_OK;
+}
+
+int sfseg_backward(sfseg_handle* h, const sfseg_neighborhood* nb, const float* grad_x, float* grad_weights,
+                   float* grad_bias, void* stream) {
+    if (int rc = check_handle(h)) return rc;
+    Taps tp;
+    if (int rc = make_taps(nb, &tp)) return rc;
+    if (!grad_x || !grad_weights || !grad_bias) return fail(SFSEG_ERR_INVALID_ARG, "null argument");
+    if (h->C < 2) return fail(SFSEG_ERR_UNSUPPORTED, "the single-channel map has no weights to learn");
+    if (!h->rec_valid || h->rec_K < 1 || h->rec_every < 1 || h->ckpt.empty())
+        return fail(SFSEG_ERR_STATE, "no recorded forward pass (power_iterate with record_every > 0)");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int K = h->rec_K, c = h->rec_every;
+    const float inv_alpha = (float)(1.0 / h->alpha), p = (float)h->p;
+    for (int i = 0; i < 2; ++i)
+        if (!h->gbuf[i]) SFSEG_CUDA(dalloc(&h->gbuf[i], (size_t)h->NP));
+    if (!h->gz) SFSEG_CUDA(dalloc(&h->gz, (size_t)h->NP));
+    while ((int)h->seg.size() < c + 1) {
+        float* q = nullptr;
+        SFSEG_CUDA(dalloc(&q, (size_t)h->NP));
+        h->seg.push_back(q);
+    }
+    if (int rc = ensure_acc(&h->dots, &h->dots_cap, K + 2)) return rc;
+    SFSEG_CUDA(cudaMemsetAsync(h->gz, 0, sizeof(float) * h->NP, s));
+    SFSEG_CUDA(cudaMemsetAsync(h->dots, 0, sizeof(double) * (K + 1), s));
+    SFSEG_CUDA(cudaMemsetAsync(h->scratch, 0, sizeof(double) * 64, s));
+    float* xK = h->ckpt.back();
+    launch_grad_in(grad_x, xK, h->rec_acc + K, h->gbuf[0], h->g, h->dots + K, s);
+    SFSEG_LAUNCHED();
+    int gi = 0;   // gbuf[gi] holds g_{k+1}
+    const int nseg = (K + c - 1) / c;
+    for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+        const int k0 = sgi * c, k1 = (k0 + c < K) ? k0 + c : K;
+        std::vector<const float*> xs((size_t)(k1 - k0 + 1));
+        xs[0] = h->ckpt[sgi];
+        for (int i = 1; i <= k1 - k0; ++i) {
+            if (k0 + i == K) {
+                xs[i] = xK;
+            } else {   // recompute x~_{k0+i} = A x_{k0+i-1} from the recorded norm
+                launch_apply(xs[i - 1], h->g.pitch, h->seg[i], h->g.pitch, h->f32, h->g, tp, inv_alpha, p,
+                             h->rec_acc + k0 + i - 1, h->scratch + 8, h->flags, s);
+                SFSEG_LAUNCHED();
+                xs[i] = h->seg[i];
+            }
+        }
+        for (int k = k1 - 1; k >= k0; --k) {
+            float* gnext = k > 0 ? h->gbuf[gi ^ 1] : nullptr;
+            launch_adjoint_step(xs[k - k0], h->rec_acc + k, xs[k + 1 - k0], h->rec_acc + k + 1, h->gbuf[gi],
+                                h->dots + k + 1, gnext, h->dots + k, h->gz, h->f32, h->g, tp, inv_alpha, p, s);
+            SFSEG_LAUNCHED();
+            gi ^= 1;
+        }
+    }
+    launch_weight_grad(h->feat_ptr, h->feat_dtype, h->C, h->g, h->gz, h->scratch + 16, s);
+    SFSEG_LAUNCHED();
+    std::vector<double> wacc((size_t)h->C + 1);
+    SFSEG_CUDA(cudaMemcpyAsync(wacc.data(), h->scratch + 16, sizeof(double) * (h->C + 1), cudaMemcpyDeviceToHost, s));
+    if (int rc = read_flags(h, s)) return rc;
+    for (int ch = 0; ch < h->C; ++ch) grad_weights[ch] = (float)wacc[ch];
+    *grad_bias = (float)wacc[h->C];
+    return SFSEG_OK;
+}
+
+int sfseg_soft_iou_loss(sfseg_handle* h, const float* x, const float* target, double* loss, float* grad_x,
+                        void* stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (!x || !target || !loss) return fail(SFSEG_ERR_INVALID_ARG, "null argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    double* a = h->scratch + 48;
+    SFSEG_CUDA(cudaMemsetAsync(a, 0, sizeof(double) * 4, s));
+    SFSEG_CUDA(cudaMemsetAsync(h->amax, 0, sizeof(unsigned long long), s));
+    launch_soft_iou(x, target, h->N, grad_x, a, h->amax, s);
+    SFSEG_LAUNCHED();
+    double hv[2];
+    SFSEG_CUDA(cudaMemcpyAsync(hv, a, sizeof(hv), cudaMemcpyDeviceToHost, s));
+    SFSEG_CUDA(cudaStreamSynchronize(s));
+    *loss = 1.0 - hv[0] / hv[1];
+    return SFSEG_OK;
+}
+
+}  // extern "C"

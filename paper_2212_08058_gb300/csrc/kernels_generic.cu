@@ -1,0 +1,298 @@
+// kernels_generic.cu -- the streaming space-time stencil for any supported radius, plus the
+// small kernels around it (channel combination, start vector, reductions).
+//
+// The Eq. 7 operator needs the 3D Gaussian filtering of three signals
+//     z1 = u x,  z2 = f^2 u x,  z3 = f u x           (u = s^p, s = f: shared maps, Sec. 5.1.2)
+// followed by the per-voxel combination
+//     A x = u [ (1/alpha - f^2) G*z1 - G*z2 + 2 f G*z3 ].
+// A CTA owns a TH x 64 tile of (h, w) and walks along t through a chunk of frames.  For each
+// incoming frame it stages the halo tile of the three signals in shared memory, filters along w
+// then h (Sec. 4.2: the separable form), and keeps the 2D-filtered frame in a ring of 2rt+1
+// frames; the t-filter and the combination then produce the output frame rt behind.
+//
+// Power iteration runs in a scaled form: the stored state is v_k = u * x~_k where x~_k = A x_{k-1}
+// is the un-normalised iterate, whose squared norm the previous launch has accumulated in FP64.
+// The Eq. 8 division by the norm is folded into the next step (A is linear), so no launch waits
+// for a global reduction, and z1 = v needs no power in the halo.
+#include <atomic>
+#include <cstdio>
+
+#include "common.cuh"
+#include "launch.h"
+#include "stencil.cuh"
+
+namespace sfseg {
+
+// ----------------------------------------------------------------------------- stencil ops
+// v-space power-iteration step.  OUT_X selects writing x~ (last step) instead of u x~.
+template <typename TVI, typename TVO, typename TF, bool OUT_X>
+struct OpIter {
+    static constexpr int NS = 3;
+    const TVI* v;
+    const TF* f;
+    TVO* out;
+    int out_pitch;
+    float* ckpt;
+    Geom g;
+    float inv_alpha, p, s;
+
+    __device__ __forceinline__ void begin(const double* acc_in, int* flags) {
+        s = inv_norm_from(acc_in, flags);
+    }
+    __device__ __forceinline__ void load(int t, int h, int w, float (&z)[NS]) const {
+        const int64_t i = ((int64_t)t * g.H + h) * g.pitch + w;
+        const float z1 = ldf(v + i), fv = ldf(f + i);
+        const float z3 = fv * z1;
+        z[0] = z1;
+        z[1] = fv * z3;
+        z[2] = z3;
+    }
+    __device__ __forceinline__ void epi(int t, int h, int w, const float (&c)[NS], float& acc0,
+                                        float&) const {
+        const int64_t i = ((int64_t)t * g.H + h) * g.pitch + w;
+        const float fv = ldf(f + i);
+        const float u = unary_pow(fv, p);
+        const float B = (inv_alpha - fv * fv) * c[0] - c[1] + 2.f * fv * c[2];
+        const float xt = s * u * B;
+        acc0 += xt * xt;
+        if (OUT_X) stf(out + ((int64_t)t * g.H + h) * out_pitch + w, xt);
+        else stf(out + i, u * xt);
+        if (ckpt) ckpt[i] = xt;
+    }
+};
+
+// x-space application y = s A x (FP32 storage), used for residuals and recomputation.
+struct OpApply {
+    static constexpr int NS = 3;
+    const float* x;
+    int x_pitch;
+    const float* f;
+    float* out;
+    int out_pitch;
+    Geom g;
+    float inv_alpha, p, s;
+
+    __device__ __forceinline__ void begin(const double* acc_in, int* flags) {
+        s = inv_norm_from(acc_in, flags);
+    }
+    __device__ __forceinline__ void load(int t, int h, int w, float (&z)[NS]) const {
+        const float xv = x[((int64_t)t * g.H + h) * x_pitch + w];
+        const float fv = f[((int64_t)t * g.H + h) * g.pitch + w];
+        const float z1 = unary_pow(fv, p) * xv;
+        const float z3 = fv * z1;
+        z[0] = z1;
+        z[1] = fv * z3;
+        z[2] = z3;
+    }
+    __device__ __forceinline__ void epi(int t, int h, int w, const float (&c)[NS], float& acc0,
+                                        float&) const {
+        const float fv = f[((int64_t)t * g.H + h) * g.pitch + w];
+        const float u = unary_pow(fv, p);
+        const float y = s * u * ((inv_alpha - fv * fv) * c[0] - c[1] + 2.f * fv * c[2]);
+        acc0 += y * y;
+        out[((int64_t)t * g.H + h) * out_pitch + w] = y;
+    }
+};
+
+static std::atomic<int64_t> g_launches{0};
+void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
+
+int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+template <typename TVI, typename TVO, typename TF, bool OUT_X>
+static void iterate_t(const void* vin, void* out, const void* f, float* ckpt, Geom g, const Taps& tp,
+                      float inv_alpha, float p, const double* acc_in, double* acc_out, int* flags,
+                      cudaStream_t s) {
+    OpIter<TVI, TVO, TF, OUT_X> op;
+    op.v = (const TVI*)vin;
+    op.f = (const TF*)f;
+    op.out = (TVO*)out;
+    op.out_pitch = OUT_X ? g.W : g.pitch;
+    op.ckpt = ckpt;
+    op.g = g;
+    op.inv_alpha = inv_alpha;
+    op.p = p;
+    op.s = 1.f;
+    run_stencil(op, tp, 16, acc_in, acc_out, nullptr, flags, s);
+}
+
+void launch_iterate(const void* vin, int vin_type, void* out, int out_type, bool out_x, const void* f,
+                    int f_type, float* ckpt, Geom g, const Taps& tp, float inv_alpha, float p,
+                    const double* acc_in, double* acc_out, int* flags, cudaStream_t s) {
+    using bf = __nv_bfloat16;
+#define SFSEG_IT(TVI, TVO, TF, OX) \
+    iterate_t<TVI, TVO, TF, OX>(vin, out, f, ckpt, g, tp, inv_alpha, p, acc_in, acc_out, flags, s)
+    // A step of the bf16 phase reads v and f in bf16 and writes bf16, or float32 when the next
+    // step (or the caller's x) is float32; a float32 step reads and writes float32.
+    (void)f_type;
+    if (out_x) {   // the last step always writes float32 x~ into the caller's layout
+        if (vin_type == kF32) SFSEG_IT(float, float, float, true);
+        else SFSEG_IT(bf, float, bf, true);
+    } else {
+        if (vin_type == kF32) SFSEG_IT(float, float, float, false);
+        else if (out_type == kBF16) SFSEG_IT(bf, bf, bf, false);
+        else SFSEG_IT(bf, float, bf, false);
+    }
+#undef SFSEG_IT
+}
+
+void launch_apply(const float* x, int x_pitch, float* y, int y_pitch, const float* f32, Geom g,
+                  const Taps& tp, float inv_alpha, float p, const double* acc_in, double* acc_out,
+                  int* flags, cudaStream_t s) {
+    OpApply op;
+    op.x = x;
+    op.x_pitch = x_pitch;
+    op.f = f32;
+    op.out = y;
+    op.out_pitch = y_pitch;
+    op.g = g;
+    op.inv_alpha = inv_alpha;
+    op.p = p;
+    op.s = 1.f;
+    run_stencil(op, tp, 16, acc_in, acc_out, nullptr, flags, s);
+}
+
+// -------------------------------------------------------------------------- Eq. 9 combine
+template <typename TIn>
+__global__ void combine_kernel(const TIn* feat, int C, Geom g, const float* w, float bias, float* f32,
+                               __nv_bfloat16* fbf, int* flags) {
+    const int64_t HW = (int64_t)g.H * g.W, N = HW * g.T;
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        float fv;
+        if (C == 1) {
+            fv = ldf(feat + i);
+        } else {
+            float z = bias;
+            for (int c = 0; c < C; ++c) z = fmaf(w[c], ldf(feat + (int64_t)c * N + i), z);
+            fv = 1.f / (1.f + expf(-z));
+        }
+        if (!(fv >= 0.f) || isinf(fv)) bad = 1;
+        const int64_t t = i / HW, rem = i - t * HW;
+        const int64_t h = rem / g.W, wc = rem - h * g.W;
+        const int64_t j = (t * g.H + h) * g.pitch + wc;
+        f32[j] = fv;
+        if (fbf) fbf[j] = __float2bfloat16_rn(fv);
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, kFlagBadFeature);
+}
+
+void launch_combine(const void* feat, int feat_dtype, int C, Geom g, const float* w_dev, float bias,
+                    float* f32, __nv_bfloat16* fbf, int* flags, cudaStream_t s) {
+    const int64_t N = (int64_t)g.T * g.H * g.W;
+    int blocks = (int)((N + 255) / 256);
+    if (blocks > 16 * num_sms()) blocks = 16 * num_sms();
+    if (feat_dtype == kF32)
+        combine_kernel<float><<<blocks, 256, 0, s>>>((const float*)feat, C, g, w_dev, bias, f32, fbf, flags);
+    else
+        combine_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>((const __nv_bfloat16*)feat, C, g, w_dev, bias,
+                                                             f32, fbf, flags);
+    count_launches(1);
+}
+
+// ------------------------------------------------------------------------- start vector
+template <typename TV>
+__global__ void prologue_kernel(int init, const float* x_user, const float* f32, float p, Geom g, TV* v0,
+                                float* x_copy, float* x_user_out, double* acc0) {
+    const int64_t HW = (int64_t)g.H * g.W, N = HW * g.T;
+    float part = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i / HW, rem = i - t * HW;
+        const int64_t h = rem / g.W, wc = rem - h * g.W;
+        const int64_t j = (t * g.H + h) * g.pitch + wc;
+        const float fv = f32[j];
+        const float x = init == 0 ? x_user[i] : (init == 1 ? 1.f : fv);
+        part += x * x;
+        stf(v0 + j, unary_pow(fv, p) * x);
+        if (x_copy) x_copy[j] = x;
+        if (x_user_out) x_user_out[i] = x;
+    }
+    const double b = block_sum((double)part);
+    if (threadIdx.x == 0) atomicAdd(acc0, b);
+}
+
+void launch_prologue(int init, const float* x_user, const float* f32, float p, Geom g, void* v0, int vtype,
+                     float* x_copy, float* x_user_out, double* acc0, cudaStream_t s) {
+    const int64_t N = (int64_t)g.T * g.H * g.W;
+    int blocks = (int)((N + 255) / 256);
+    if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
+    if (vtype == kF32)
+        prologue_kernel<float><<<blocks, 256, 0, s>>>(init, x_user, f32, p, g, (float*)v0, x_copy, x_user_out, acc0);
+    else
+        prologue_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(init, x_user, f32, p, g, (__nv_bfloat16*)v0, x_copy,
+                                                              x_user_out, acc0);
+    count_launches(1);
+}
+
+__global__ void to_bf16_kernel(const float* a, __nv_bfloat16* b, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = __float2bfloat16_rn(a[i]);
+}
+
+void launch_to_bf16(const float* a, __nv_bfloat16* b, int64_t n, cudaStream_t s) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 16 * num_sms()) blocks = 16 * num_sms();
+    to_bf16_kernel<<<blocks, 256, 0, s>>>(a, b, n); count_launches(1);
+}
+
+// ------------------------------------------------------------------------- reductions
+__global__ void scale_inv_norm_kernel(float* x, int64_t n, const double* acc, int* flags) {
+    const float s = inv_norm_from(acc, flags);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] *= s;
+}
+
+void launch_scale_inv_norm(float* x, int64_t n, const double* acc, int* flags, cudaStream_t s) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
+    scale_inv_norm_kernel<<<blocks, 256, 0, s>>>(x, n, acc, flags); count_launches(1);
+}
+
+__global__ void dot2_kernel(const float* x, const float* y, int64_t n, double* acc) {
+    float a = 0.f, b = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        a += x[i] * y[i];
+        b += x[i] * x[i];
+    }
+    const double sa = block_sum((double)a);
+    if (threadIdx.x == 0) atomicAdd(acc, sa);
+    const double sb = block_sum((double)b);
+    if (threadIdx.x == 0) atomicAdd(acc + 1, sb);
+}
+
+__global__ void resid_kernel(const float* x, const float* y, int64_t n, double* acc) {
+    const float rho = (float)(acc[0] / acc[1]);
+    float a = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float d = y[i] - rho * x[i];
+        a += d * d;
+    }
+    const double sa = block_sum((double)a);
+    if (threadIdx.x == 0) atomicAdd(acc + 2, sa);
+}
+
+void launch_dot2(const float* x, const float* y, int64_t n, double* acc, cudaStream_t s) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
+    dot2_kernel<<<blocks, 256, 0, s>>>(x, y, n, acc); count_launches(1);
+}
+
+void launch_resid(const float* x, const float* y, int64_t n, double* acc, cudaStream_t s) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
+    resid_kernel<<<blocks, 256, 0, s>>>(x, y, n, acc); count_launches(1);
+}
+
+}  // namespace sfseg

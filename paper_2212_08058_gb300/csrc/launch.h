@@ -1,0 +1,69 @@
+// launch.h -- host-side launchers of the sfseg kernels (internal to libsfseg.so).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace sfseg {
+
+enum StoreType { kF32 = 0, kBF16 = 1 };
+
+// Eq. 9 / Alg. 1 lines 1-2: features [C][T][H][W] (caller layout) -> f (internal pitch), in
+// float32 and, when fbf != nullptr, also in bf16.
+void launch_combine(const void* feat, int feat_dtype, int C, Geom g, const float* w_dev, float bias,
+                    float* f32, __nv_bfloat16* fbf, int* flags, cudaStream_t s);
+
+// Start vector (Alg. 1 line 3 or uniform or the caller's x): writes v0 = u x0 (internal, in
+// `vtype`), acc[0] = ||x0||^2, and optionally an FP32 copy of x0 (internal pitch) and x0 into
+// the caller's layout.
+void launch_prologue(int init, const float* x_user, const float* f32, float p, Geom g, void* v0,
+                     int vtype, float* x_copy, float* x_user_out, double* acc0, cudaStream_t s);
+
+// One Eq. 7 power-iteration step in the scaled, u-weighted form (see kernels_generic.cu):
+// input v_k = u x~_k (internal), output v_{k+1} = u x~_{k+1} or, when `out_x`, x~_{k+1} itself
+// in the caller's layout (pitch W).  acc_in = ||x~_k||^2, acc_out += ||x~_{k+1}||^2.
+// `ckpt` (nullable) receives an FP32 copy of x~_{k+1} in internal layout.
+void launch_iterate(const void* vin, int vin_type, void* out, int out_type, bool out_x,
+                    const void* f, int f_type, float* ckpt, Geom g, const Taps& tp,
+                    float inv_alpha, float p, const double* acc_in, double* acc_out, int* flags,
+                    cudaStream_t s);
+
+// y = s * A x in the plain (x-space) form: x with pitch x_pitch, y with pitch y_pitch, FP32
+// features; s = 1/sqrt(*acc_in) (or 1 if acc_in is null); acc_out += ||y||^2 (nullable).
+void launch_apply(const float* x, int x_pitch, float* y, int y_pitch, const float* f32, Geom g,
+                  const Taps& tp, float inv_alpha, float p, const double* acc_in, double* acc_out,
+                  int* flags, cudaStream_t s);
+
+// bf16 copy of a float32 array (n elements).
+void launch_to_bf16(const float* a, __nv_bfloat16* b, int64_t n, cudaStream_t s);
+
+// x *= 1/sqrt(*acc) over a caller-layout volume.
+void launch_scale_inv_norm(float* x, int64_t n, const double* acc, int* flags, cudaStream_t s);
+
+// acc[0] += sum x*y, acc[1] += sum x*x  (x, y caller layout, n elements)
+void launch_dot2(const float* x, const float* y, int64_t n, double* acc, cudaStream_t s);
+// acc[2] += sum (y - rho x)^2 with rho = acc[0] / acc[1]
+void launch_resid(const float* x, const float* y, int64_t n, double* acc, cudaStream_t s);
+
+// Backward (adjoint) pieces, see kernels_bwd.cu.
+void launch_grad_in(const float* gx_user, const float* xK, const double* accK, float* g_out, Geom g,
+                    double* dot_out, cudaStream_t s);
+void launch_adjoint_step(const float* xk, const double* acc_k, const float* xn, const double* acc_n,
+                         const float* gn, const double* dot_n, float* gk_out, double* dot_k,
+                         float* gz, const float* f32, Geom g, const Taps& tp, float inv_alpha,
+                         float p, cudaStream_t s);
+void launch_weight_grad(const void* feat, int feat_dtype, int C, Geom g, const float* gz,
+                        double* acc_c_plus_1, cudaStream_t s);
+void launch_soft_iou(const float* x, const float* tgt, int64_t n, float* grad, double* acc,
+                     unsigned long long* amax, cudaStream_t s);
+
+int num_sms();
+
+// Process-wide count of kernels launched by the library (sfseg_kernel_launches).
+void count_launches(int n);
+int64_t launches_so_far();
+
+}  // namespace sfseg

@@ -1,0 +1,274 @@
+"""Thin Python binding of libsfseg.so (include/sfseg.h): argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels; PyTorch provides device
+memory and the current stream.  There is no CPU fallback: if the library is missing this module
+raises instead of computing anything.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsfseg.so")
+
+SFSEG_F32, SFSEG_BF16 = 0, 1
+INIT = {"user": 0, "uniform": 1, "smap": 2}
+STATUS = {0: "OK", 1: "INVALID_ARG", 2: "SHAPE", 3: "DTYPE", 4: "CUDA", 5: "OOM", 6: "TIMEOUT",
+          7: "NONFINITE", 8: "ZERO_NORM", 9: "STATE", 10: "UNSUPPORTED"}
+
+_lib = None
+
+
+class SFSegError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"sfseg error {STATUS.get(code, code)}: {msg}")
+        self.code = code
+        self.status = STATUS.get(code, str(code))
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("alpha", ctypes.c_double), ("p", ctypes.c_double)]
+
+
+class Neighborhood(ctypes.Structure):
+    _fields_ = [("rt", ctypes.c_int), ("rh", ctypes.c_int), ("rw", ctypes.c_int),
+                ("sigma_t", ctypes.c_float), ("sigma_h", ctypes.c_float), ("sigma_w", ctypes.c_float)]
+
+
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_f = ctypes.c_float
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+
+# (name, argtypes) of every entry point declared in include/sfseg.h
+SIGNATURES = {
+    "sfseg_version": [],
+    "sfseg_last_error": [],
+    "sfseg_create": [ctypes.POINTER(Params), _i, _i, _i, _i, ctypes.POINTER(_vp)],
+    "sfseg_destroy": [_vp],
+    "sfseg_set_features": [_vp, _vp, _i, _fp, _f, _vp],
+    "sfseg_power_iterate": [_vp, _vp, _i, _fp, _f, ctypes.POINTER(Neighborhood), _i, _i, _vp, _i, _i,
+                            _dp, _vp],
+    "sfseg_apply": [_vp, ctypes.POINTER(Neighborhood), _vp, _vp, _vp],
+    "sfseg_rayleigh": [_vp, ctypes.POINTER(Neighborhood), _vp, _dp, _dp, _vp],
+    "sfseg_backward": [_vp, ctypes.POINTER(Neighborhood), _vp, _fp, _fp, _vp],
+    "sfseg_soft_iou_loss": [_vp, _vp, _vp, _dp, _vp, _vp],
+    "sfseg_enable_iter_timing": [_vp, _i],
+    "sfseg_iter_timing": [_vp, _dp, ctypes.POINTER(ctypes.c_int64)],
+    "sfseg_kernel_launches": [ctypes.POINTER(ctypes.c_int64)],
+}
+
+
+def lib(path: str | None = None):
+    """Load libsfseg.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"{p} is missing: build it with paper_2212_08058_gb300.build.build() "
+                               "(there is no fallback implementation)")
+        L = ctypes.CDLL(p)
+        for name, args in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.sfseg_last_error.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise SFSegError(rc, lib().sfseg_last_error().decode())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return SFSEG_F32
+    if t.dtype == torch.bfloat16:
+        return SFSEG_BF16
+    raise TypeError(f"unsupported dtype {t.dtype}: float32 or bfloat16")
+
+
+def default_sigma(radius) -> tuple:
+    """Isotropic Gaussian width sigma = max(radius) / 2 (1.0 when every radius is 0)."""
+    s = max(radius) / 2.0 or 1.0
+    return (s, s, s)
+
+
+def neighborhood(radius, sigma=None) -> Neighborhood:
+    rt, rh, rw = (int(r) for r in radius)
+    st, sh, sw = default_sigma(radius) if sigma is None else sigma
+    return Neighborhood(rt, rh, rw, float(st), float(sh), float(sw))
+
+
+def _host_floats(w, n: int):
+    if w is None:
+        return None, None
+    a = np.ascontiguousarray(np.asarray(w.detach().cpu() if torch.is_tensor(w) else w, dtype=np.float32))
+    if a.size != n:
+        raise ValueError(f"expected {n} channel weights, got {a.size}")
+    return a, a.ctypes.data_as(_fp)
+
+
+class PowerIteration:
+    """A handle of the library for C-channel volumes of T x H x W voxels (sfseg_create)."""
+
+    def __init__(self, C: int, T: int, H: int, W: int, alpha: float = 1.0, p: float = 0.1):
+        self.shape = (C, T, H, W)
+        self.C, self.T, self.H, self.W = C, T, H, W
+        self.alpha, self.p = alpha, p
+        h = ctypes.c_void_p()
+        _check(lib().sfseg_create(ctypes.byref(Params(alpha, p)), C, T, H, W, ctypes.byref(h)))
+        self._h = h
+        self._features = None
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().sfseg_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ----------------------------------------------------------------------------------
+    def _check_features(self, features: torch.Tensor):
+        if not features.is_cuda or not features.is_contiguous():
+            raise ValueError("features must be a contiguous CUDA tensor")
+        if tuple(features.shape) != self.shape:
+            raise ValueError(f"features shape {tuple(features.shape)} != {self.shape}")
+
+    def _check_volume(self, x: torch.Tensor, name: str):
+        if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+        if x.numel() != self.T * self.H * self.W:
+            raise ValueError(f"{name} has {x.numel()} elements, expected {self.T * self.H * self.W}")
+
+    def set_features(self, features: torch.Tensor, weights=None, bias: float = 0.0):
+        self._check_features(features)
+        _, wp = _host_floats(weights, self.C)
+        _check(lib().sfseg_set_features(self._h, _ptr(features), _dtype_code(features), wp, float(bias),
+                                        _stream()))
+        self._features = features
+
+    def power_iterate(self, features: torch.Tensor | None = None, weights=None, bias: float = 0.0,
+                      radius=(2, 7, 7), sigma=None, iters: int = 50, iters_bf16: int = 0,
+                      x: torch.Tensor | None = None, init: str = "uniform", record_every: int = 0,
+                      return_norms: bool = False):
+        """Run ``iters`` power iterations; returns the unit-norm x [T, H, W] (and the norms
+        nu_k = ||A x_{k-1}|| when ``return_norms``, which synchronises)."""
+        if features is not None:
+            self._check_features(features)
+            self._features = features
+        _, wp = _host_floats(weights, self.C) if features is not None else (None, None)
+        if x is None:
+            x = torch.empty((self.T, self.H, self.W), device="cuda", dtype=torch.float32)
+            if init == "user":
+                raise ValueError("init='user' needs x")
+        else:
+            self._check_volume(x, "x")
+        nb = neighborhood(radius, sigma)
+        norms = np.empty(max(iters, 1)) if return_norms else None
+        _check(lib().sfseg_power_iterate(
+            self._h, _ptr(features), _dtype_code(features) if features is not None else 0, wp, float(bias),
+            ctypes.byref(nb), int(iters), int(iters_bf16), _ptr(x), INIT[init], int(record_every),
+            norms.ctypes.data_as(_dp) if norms is not None else None, _stream()))
+        return (x, norms[:iters]) if return_norms else x
+
+    def apply(self, x: torch.Tensor, radius=(2, 7, 7), sigma=None) -> torch.Tensor:
+        """y = A x (the Eq. 7 operator, FP32)."""
+        self._check_volume(x, "x")
+        y = torch.empty_like(x)
+        _check(lib().sfseg_apply(self._h, ctypes.byref(neighborhood(radius, sigma)), _ptr(x), _ptr(y), _stream()))
+        return y
+
+    def rayleigh(self, x: torch.Tensor, radius=(2, 7, 7), sigma=None):
+        """(rho, residual) of x for the FP32 operator; synchronises."""
+        self._check_volume(x, "x")
+        rho = ctypes.c_double()
+        res = ctypes.c_double()
+        _check(lib().sfseg_rayleigh(self._h, ctypes.byref(neighborhood(radius, sigma)), _ptr(x),
+                                    ctypes.byref(rho), ctypes.byref(res), _stream()))
+        return rho.value, res.value
+
+    def backward(self, grad_x: torch.Tensor, radius=(2, 7, 7), sigma=None):
+        """(dL/dw [C] numpy float32, dL/db float) for the last recorded power_iterate call."""
+        self._check_volume(grad_x, "grad_x")
+        gw = np.zeros(self.C, dtype=np.float32)
+        gb = ctypes.c_float()
+        _check(lib().sfseg_backward(self._h, ctypes.byref(neighborhood(radius, sigma)), _ptr(grad_x),
+                                    gw.ctypes.data_as(_fp), ctypes.byref(gb), _stream()))
+        return gw, gb.value
+
+    def soft_iou_loss(self, x: torch.Tensor, target: torch.Tensor, grad: bool = True):
+        """(1 - soft-IoU(x / max x, target), dL/dx or None); synchronises."""
+        self._check_volume(x, "x")
+        self._check_volume(target, "target")
+        g = torch.empty_like(x) if grad else None
+        loss = ctypes.c_double()
+        _check(lib().sfseg_soft_iou_loss(self._h, _ptr(x), _ptr(target), ctypes.byref(loss), _ptr(g), _stream()))
+        return loss.value, g
+
+
+    def enable_iter_timing(self, on: bool = True):
+        _check(lib().sfseg_enable_iter_timing(self._h, int(bool(on))))
+
+    def iter_timing(self):
+        """(milliseconds, launches) of the iteration kernels since the last read (CUDA events)."""
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        _check(lib().sfseg_iter_timing(self._h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+
+def kernel_launches() -> int:
+    """Kernels launched by libsfseg.so in this process so far."""
+    n = ctypes.c_int64()
+    _check(lib().sfseg_kernel_launches(ctypes.byref(n)))
+    return n.value
+
+
+class SFSegFunction(torch.autograd.Function):
+    """x_K = SFSeg++(features; w, b) as a differentiable function of the channel weights and bias
+    (Sec. 3.4): the forward records checkpoints, the backward runs the library's adjoint."""
+
+    @staticmethod
+    def forward(ctx, weights, bias, features, handle: PowerIteration, radius, sigma, iters, record_every):
+        x = handle.power_iterate(features, weights.detach().cpu().numpy(), float(bias), radius, sigma, iters,
+                                 record_every=record_every)
+        ctx.handle, ctx.radius, ctx.sigma = handle, radius, sigma
+        ctx.wdev, ctx.bdev = weights.device, bias.device if torch.is_tensor(bias) else None
+        return x
+
+    @staticmethod
+    def backward(ctx, grad_x):
+        gw, gb = ctx.handle.backward(grad_x.contiguous(), ctx.radius, ctx.sigma)
+        gw_t = torch.from_numpy(gw).to(ctx.wdev)
+        gb_t = torch.tensor(gb, dtype=torch.float32, device=ctx.bdev) if ctx.bdev is not None else None
+        return gw_t, gb_t, None, None, None, None, None, None
+
+
+def sfseg_pp(weights, bias, features, handle, radius=(1, 3, 3), sigma=None, iters=30, record_every=5):
+    return SFSegFunction.apply(weights, bias, features, handle, radius, sigma, iters, record_every)

@@ -30,8 +30,8 @@ MUTANTS = [
      ["test_combine_sigmoid_is_logistic"]),
     ("gradient_pair_sign", "- 2.0 * alpha * ua * ub * d;", "+ 2.0 * alpha * ua * ub * d;",
      ["test_grad_matches_finite_differences"]),
-    ("wrap_padding", "if (tt < 0 || tt >= T || hh < 0 || hh >= H || ww < 0 || ww >= W) continue;",
-     "tt = (tt + T) % T; hh = (hh + H) % H; ww = (ww + W) % W;",
+    ("edge_padding_off_by_one", "int lo = pos - r < 0 ? -pos : -r;",
+     "int lo = pos - r < 0 ? 1 - pos : -r;",
      ["test_filter_form_equals_explicit_matrix"]),
     ("l1_renormalisation",
      "orc_spmv(N, rowptr, col, val, x_out, y);\n        double nu = sqrt(orc_sumsq(y, N));",
