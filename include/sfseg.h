@@ -156,6 +156,36 @@ int sfseg_iter_timing(sfseg_handle* h, double* ms, int64_t* launches);
 /* Number of CUDA kernels this library has launched in the process so far (host output). */
 int sfseg_kernel_launches(int64_t* count);
 
+/* No-allocation power iteration (the paper has no counterpart: this is a deployment aid).
+ *
+ * For callers that cannot allocate device memory -- a server that reserves its whole memory
+ * budget at start-up and forbids later cudaMalloc calls, a latency-bound loop where cudaMalloc
+ * or cudaFree would synchronise the device and stall other streams, or plug-in code that keeps
+ * no handle to own a workspace.  It computes what sfseg_create + sfseg_power_iterate (float32
+ * storage, no recording) + sfseg_destroy compute, with the same kernels, but allocates nothing:
+ * its scratch (combined features, two iterate buffers, FP64 norms, flags, weights) is one fixed
+ * array of about 24 MiB in device global memory, declared by the library, which every GPU that
+ * loads libsfseg.so holds until the process exits.
+ *   Limits: T * H * round_up(W, 32) <= SFSEG_NOALLOC_MAX_VOXELS and 0 <= iters <=
+ *   SFSEG_NOALLOC_MAX_ITERS; larger requests return SFSEG_ERR_SHAPE / SFSEG_ERR_INVALID_ARG
+ *   without touching the GPU.
+ *   Arguments: as sfseg_create (prm, C, T, H, W) and sfseg_power_iterate (features, dtype,
+ *   weights, bias, nb, iters, x_inout, init, norms_out, stream).  The caller owns features,
+ *   x_inout and norms_out.
+ *   Sharing: every call, from any thread, on any stream of the same device, uses the same
+ *   array, which keeps the previous call's contents (the call clears what must start at
+ *   zero).  Calls whose GPU work overlaps -- concurrent streams, or calls on one device from
+ *   several threads without ordering -- race on it and give wrong results; order them.
+ *   Set-up: the first call on each device (with that device current) looks up the array's
+ *   device address with cudaGetSymbolAddress; make that first call before any stream capture
+ *   begins on the device. */
+#define SFSEG_NOALLOC_MAX_VOXELS 2097152
+#define SFSEG_NOALLOC_MAX_ITERS 4096
+int sfseg_power_iterate_noalloc(const sfseg_params* prm, int C, int T, int H, int W,
+                                const void* features, int dtype, const float* weights, float bias,
+                                const sfseg_neighborhood* nb, int iters, float* x_inout, int init,
+                                double* norms_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

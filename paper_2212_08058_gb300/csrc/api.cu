@@ -43,6 +43,10 @@ cudaError_t dalloc(T** p, size_t n) {
 
 }  // namespace
 
+namespace sfseg {
+int set_last_error(int code, const char* msg) { return fail(code, msg); }
+}  // namespace sfseg
+
 struct sfseg_handle {
     int C = 0;
     double alpha = 1.0, p = 0.1;

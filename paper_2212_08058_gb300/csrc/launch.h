@@ -62,6 +62,9 @@ void launch_soft_iou(const float* x, const float* tgt, int64_t n, float* grad, d
 
 int num_sms();
 
+// Records `msg` as the thread's sfseg_last_error() text and returns `code`.
+int set_last_error(int code, const char* msg);
+
 // Process-wide count of kernels launched by the library (sfseg_kernel_launches).
 void count_launches(int n);
 int64_t launches_so_far();

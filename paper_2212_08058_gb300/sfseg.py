@@ -61,6 +61,8 @@ SIGNATURES = {
     "sfseg_enable_iter_timing": [_vp, _i],
     "sfseg_iter_timing": [_vp, _dp, ctypes.POINTER(ctypes.c_int64)],
     "sfseg_kernel_launches": [ctypes.POINTER(ctypes.c_int64)],
+    "sfseg_power_iterate_noalloc": [ctypes.POINTER(Params), _i, _i, _i, _i, _vp, _i, _fp, _f,
+                                    ctypes.POINTER(Neighborhood), _i, _vp, _i, _dp, _vp],
 }
 
 
