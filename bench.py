@@ -31,8 +31,9 @@ RADIUS = (2, 7, 7)
 ITERS = 50
 SEED = 2000
 WORKLOAD = "plain SFSeg 480p: C=1 fp32 64x480x854, three crossing blobs, radius (2,7,7), 50 iterations"
-PROFILE_FILE = os.path.join(ROOT, "profiles", "iterate_f32_r277_480p.txt")
-KERNEL_SOURCES = ["stencil.cuh", "kernels_generic.cu", "common.cuh"]
+PROFILE_FILE = os.path.join(ROOT, "profiles", "iter_fast_r277_f32_480p.txt")
+KERNEL_SOURCES = ["kernels_fast.cu", "common.cuh"]
+FMA_PER_VOXEL = 3 * ((2 * RADIUS[0] + 1) + (2 * RADIUS[1] + 1) + (2 * RADIUS[2] + 1))   # 105 at (2,7,7)
 
 
 def _peaks():
@@ -125,6 +126,24 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def rank_seed(rank: int) -> int:
+    """Each rank times its own volume (independent problems, no data-path collective)."""
+    return SEED + rank
+
+
+def aggregate(ms_local: float, units_per_step_per_rank: float, steps: int, world: int, device=None):
+    """Whole-job throughput: the slowest rank's time (max over ranks) for the units all ranks
+    processed.  Returns (units/s, max ms)."""
+    ms = ms_local
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return world * units_per_step_per_rank * steps / (ms * 1e-3), ms
+
+
 def cpu_baseline(seconds_budget: float = 20.0):
     """The FP64 oracle (filter form, OpenMP) on the host cores: a bounded sample of the same
     workload -- as many whole Eq. 7 + Eq. 8 iterations of the full 64 x 480 x 854 volume as fit
@@ -176,6 +195,55 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
+def bench_bf16_multichannel(sfseg, synth, steps: int = 10):
+    """SFSeg++ with bf16 storage: C = 8 bf16 channels of 64 x 480 x 854 (the multichannel recipe,
+    drawn on the device), radius (2,7,7), 50 iterations all in bf16 storage.  Device-resident
+    voxel-iterations/s, CUDA events."""
+    import torch
+    V, w = synth.multichannel_torch(T, H, W, 8, seed=3000, device="cuda", dtype=torch.bfloat16)
+    w = w.cpu().numpy()
+    h = sfseg.PowerIteration(8, T, H, W)
+    x = torch.empty((T, H, W), device="cuda")
+    for _ in range(3):
+        h.power_iterate(V, w, 0.0, RADIUS, iters=ITERS, iters_bf16=ITERS, x=x)
+    torch.cuda.synchronize()
+    h.enable_iter_timing(True)
+    h.iter_timing()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        h.power_iterate(V, w, 0.0, RADIUS, iters=ITERS, iters_bf16=ITERS, x=x)
+    e1.record()
+    torch.cuda.synchronize()
+    it_ms, it_n = h.iter_timing()
+    h.close()
+    nvox = T * H * W
+    return {"workload": "SFSeg++ C=8 bf16 64x480x854, radius (2,7,7), 50 iterations in bf16 storage",
+            "value": nvox * ITERS * steps / (e0.elapsed_time(e1) * 1e-3), "unit": UNIT,
+            "avg_launch_ms": it_ms / max(it_n, 1),
+            "hbm_frac_of_measured": 6.0 * nvox / (it_ms * 1e-3 / max(it_n, 1)) / 1e9 / _peaks()[0]}
+
+
+def bench_time_to_residual(sfseg, synth, warmstart, tol: float = 1e-4):
+    """Wall time to the Eq. 3 residual tol on the C = 8 bf16 120 x 1080 x 1920 volume from three
+    starts: uniform with float32 storage, S_m with float32 storage, and the trained warm-start
+    network followed by bf16 storage until the residual reaches 2e-3, then float32."""
+    import torch
+    T5, H5, W5 = 120, 1080, 1920
+    V, _ = synth.multichannel_torch(T5, H5, W5, 8, seed=5500, device="cuda", dtype=torch.bfloat16)
+    w = synth.fixed_weights(8)
+    net = sfseg.WarmStartNet(8)
+    trained = warmstart.load(net)
+    res = warmstart.compare_starts(V, w, RADIUS, tol=tol, net=net if trained else None, max_iters=3000)
+    net.close()
+    del V
+    torch.cuda.empty_cache()
+    res["volume"] = "C=8 bf16 120x1080x1920 (multichannel recipe on the device), radius (2,7,7)"
+    res["tol"] = tol
+    res["warmstart_trained"] = trained
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -183,6 +251,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the bf16 and time-to-residual lines")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -203,7 +272,7 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     # inputs: each rank its own volume (independent problems; no data-path collective)
-    V = synth.crossing_blobs(T, H, W, seed=SEED + rank)
+    V = synth.crossing_blobs(T, H, W, seed=rank_seed(rank))
     feats = torch.from_numpy(V).cuda()
     feats_host = torch.from_numpy(V).pin_memory()
     nvox = T * H * W
@@ -236,12 +305,11 @@ def main():
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     launches = sfseg.kernel_launches() - n_launch0
+    clk_summary = clk.summary()
     it_ms, it_n = h.iter_timing()
     h.enable_iter_timing(False)
+    value, ms = aggregate(ms, nvox * ITERS, args.steps, world, device="cuda")
     if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     torch.cuda.synchronize()
 
@@ -262,18 +330,20 @@ def main():
     e1.record(stream)
     torch.cuda.synchronize()
     ems = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([ems], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ems = float(t.item())
+    evalue, ems = aggregate(ems, nvox * ITERS, args.steps, world, device="cuda")
 
     if rank == 0:
-        value = world * nvox * ITERS * args.steps / (ms * 1e-3)
-        evalue = world * nvox * ITERS * args.steps / (ems * 1e-3)
         peak, peak_kind = _peaks()
         per_launch_s = it_ms * 1e-3 / max(it_n, 1)
         algo_bytes = 12.0 * nvox              # read v and f, write v: float32, per iteration launch
         achieved = algo_bytes / per_launch_s / 1e9
+        # At radius (2,7,7) the step needs 105 FMA per 12 bytes, above the GPU's balance of
+        # FP32 FMA rate to HBM bandwidth, so the FP32 pipe is the roof: 128 FMA per clock per
+        # SM (measured: FFMA2 does not raise it), 2 flops per FMA, at the sampled SM clock.
+        clk = clk_summary["sm_mhz"] if clk_summary else 2070.0
+        nsm = torch.cuda.get_device_properties(local).multi_processor_count
+        alu_peak = nsm * 128 * 2 * clk * 1e6 / 1e12
+        alu_achieved = 2.0 * FMA_PER_VOXEL * nvox / per_launch_s / 1e12
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -282,19 +352,26 @@ def main():
             "config": {"workload": WORKLOAD, "T": T, "H": H, "W": W, "C": 1, "radius": list(RADIUS),
                        "iters": ITERS, "storage": "f32",
                        "l2": "inputs larger than L2 (f + two iterate buffers = 318 MB > 129 MB)"},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": profiled_traffic(),
-                         "kernel": "stream_stencil<OpIter<float,float,float>>",
-                         "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes,
-                         "avg_launch_ms": per_launch_s * 1e3},
+            "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": alu_achieved / alu_peak, "traffic": profiled_traffic(),
+                         "kernel": "iter_fast<2,7,7,float,float>",
+                         "peak_kind": f"derived: {nsm} SMs x 128 FP32 lanes x 2 flop x {clk:.0f} MHz",
+                         "algorithmic_flops_per_launch": 2.0 * FMA_PER_VOXEL * nvox,
+                         "avg_launch_ms": per_launch_s * 1e3,
+                         "hbm": {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                                 "peak_kind": peak_kind, "algorithmic_bytes_per_launch": algo_bytes}},
             "e2e": {"value": evalue, "unit": UNIT, "h2d_bytes_per_step": nvox * 4,
                     "d2h_bytes_per_step": nvox * 4},
             "gpu_launches": launches,
-            "clocks": clk.summary(),
+            "clocks": clk_summary,
             "residual": res, "rho": rho,
             "paper_context": "0.01 s per iteration per 480x854 frame on a GTX Titan X (Maxwell), "
                              "about 4.1e7 voxel-iterations/s (Sec. 5, running time)",
         }
+        if world == 1 and not args.no_extras:
+            from paper_2212_08058_gb300 import warmstart
+            out["bf16_multichannel"] = bench_bf16_multichannel(sfseg, synth)
+            out["time_to_residual"] = bench_time_to_residual(sfseg, synth, warmstart)
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
         print(json.dumps(out), flush=True)

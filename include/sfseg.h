@@ -39,7 +39,8 @@ typedef enum sfseg_status {
     SFSEG_ERR_DTYPE = 3,       /* unknown dtype code */
     SFSEG_ERR_CUDA = 4,        /* a CUDA runtime call failed (message holds the CUDA error) */
     SFSEG_ERR_OOM = 5,         /* device allocation failed */
-    SFSEG_ERR_TIMEOUT = 6,     /* a bounded device-side wait gave up */
+    SFSEG_ERR_TIMEOUT = 6,     /* a bounded device-side wait (TMA copy) gave up; reported by the
+                                  next synchronising call */
     SFSEG_ERR_NONFINITE = 7,   /* a feature is negative, NaN or Inf, or a norm became non-finite */
     SFSEG_ERR_ZERO_NORM = 8,   /* an iterate became exactly zero (e.g. u = 0 everywhere) */
     SFSEG_ERR_STATE = 9,       /* call order violated (no features set, no recorded forward, ...) */
@@ -144,6 +145,50 @@ int sfseg_backward(sfseg_handle* h, const sfseg_neighborhood* nb, const float* g
  * loss: host double.  Synchronises. */
 int sfseg_soft_iou_loss(sfseg_handle* h, const float* x, const float* target, double* loss,
                         float* grad_x, void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Learned warm start (no counterpart in the paper, which starts from a uniform vector or from
+ * S_m, Alg. 1 line 3).  A 4-layer 3x3x3 convolutional network, C_in -> 32 -> 32 -> 32 -> 1, ReLU
+ * between layers and softplus at the end, predicts a start vector x0 > 0 from the raw input
+ * channels.  Forward and data-gradient convolutions run on the tensor cores (bf16 in, fp32
+ * accumulation); parameters are fp32 with AdamW.  Parameter order in the flat host vectors:
+ * W1[32][3][3][3][C_in], b1[32], W2[32][3][3][3][32], b2[32], W3 (same), b3, W4[1][3][3][3][32], b4[1]
+ * (weights as [out][kt][kh][kw][in], cross-correlation, zero padding 1).
+ * ---------------------------------------------------------------------------------------- */
+typedef struct sfseg_net sfseg_net;
+
+/* Create a network for 1 <= c_in <= 16 input channels with He-normal weights drawn from a
+ * counter-based generator seeded by `seed`, zero biases.  Allocates its parameters, gradients
+ * and AdamW moments on the current device; activation workspace grows with the largest volume
+ * seen (about 240 bytes per voxel). */
+int sfseg_net_create(int c_in, uint64_t seed, sfseg_net** out);
+int sfseg_net_destroy(sfseg_net* net);
+int sfseg_net_num_params(sfseg_net* net, int64_t* count);
+/* Copy all parameters to / from a host float array of sfseg_net_num_params entries. */
+int sfseg_net_get_params(sfseg_net* net, float* host, int64_t count);
+int sfseg_net_set_params(sfseg_net* net, const float* host, int64_t count);
+
+/* x0_out (device float32 [T][H][W]) = network(features), features device [C][T][H][W] in
+ * `dtype` with C <= c_in.  Asynchronous. */
+int sfseg_net_forward(sfseg_net* net, const void* features, int dtype, int C, int T, int H, int W,
+                      float* x0_out, void* stream);
+
+/* Training loss and gradients: L = 1 - <x0, target> / (||x0|| ||target||) for the network's x0
+ * (the direction of the start vector is what power iteration uses).  target: device float32
+ * [T][H][W].  Writes L to *loss (host) and, if grads_out is not NULL, the parameter gradients to
+ * it (host, sfseg_net_num_params floats); keeps them for sfseg_net_adamw.  Synchronises. */
+int sfseg_net_backward(sfseg_net* net, const void* features, int dtype, int C, int T, int H, int W,
+                       const float* target, double* loss, float* grads_out, void* stream);
+
+/* One AdamW step (decoupled weight decay) with the gradients of the last sfseg_net_backward. */
+int sfseg_net_adamw(sfseg_net* net, float lr, float beta1, float beta2, float eps,
+                    float weight_decay, void* stream);
+
+/* The start vector for this handle's volume: x0_out (device float32 [T][H][W], usable as
+ * x_inout with SFSEG_INIT_USER) = network(features), features device [C][T][H][W] of the
+ * handle's shape in `dtype`.  Asynchronous. */
+int sfseg_warmstart(sfseg_handle* h, sfseg_net* net, const void* features, int dtype, float* x0_out,
+                    void* stream);
 
 /* Instrumentation (no counterpart in the paper).  When enabled, each sfseg_power_iterate call
  * records two CUDA events on its stream, before its first and after its last iteration-kernel

@@ -136,6 +136,7 @@ static int read_flags(sfseg_handle* h, cudaStream_t s) {
     SFSEG_CUDA(cudaMemcpyAsync(&fl, h->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
     SFSEG_CUDA(cudaStreamSynchronize(s));
     if (fl) SFSEG_CUDA(cudaMemsetAsync(h->flags, 0, sizeof(int), s));
+    if (fl & kFlagTimeout) return fail(SFSEG_ERR_TIMEOUT, "a bounded wait for a TMA copy gave up");
     if (fl & kFlagBadFeature) return fail(SFSEG_ERR_NONFINITE, "features must be finite and >= 0");
     if (fl & kFlagNonfinite) return fail(SFSEG_ERR_NONFINITE, "an iterate norm became NaN or Inf");
     if (fl & kFlagZeroNorm) return fail(SFSEG_ERR_ZERO_NORM, "an iterate became zero (u = 0 on its support?)");
@@ -359,6 +360,11 @@ int sfseg_iter_timing(sfseg_handle* h, double* ms, int64_t* launches) {
     return SFSEG_OK;
 }
 
+int sfseg_warmstart(sfseg_handle* h, sfseg_net* net, const void* features, int dtype, float* x0_out, void* stream) {
+    if (int rc = check_handle(h)) return rc;
+    return sfseg_net_forward(net, features, dtype, h->C, h->g.T, h->g.H, h->g.W, x0_out, stream);
+}
+
 int sfseg_kernel_launches(int64_t* count) {
     if (!count) return fail(SFSEG_ERR_INVALID_ARG, "null argument");
     *count = launches_so_far();
@@ -372,8 +378,8 @@ int sfseg_apply(sfseg_handle* h, const sfseg_neighborhood* nb, const float* x, f
     if (!x || !y) return fail(SFSEG_ERR_INVALID_ARG, "null x or y");
     if (x == y) return fail(SFSEG_ERR_INVALID_ARG, "x and y must not alias");
     if (!h->features_set) return fail(SFSEG_ERR_STATE, "no features set");
-    launch_apply(x, h->g.W, y, h->g.W, h->f32, h->g, tp, (float)(1.0 / h->alpha), (float)h->p, nullptr, nullptr,
-                 h->flags, (cudaStream_t)stream);
+    launch_apply_user(x, y, (float*)h->vbuf[1], h->f32, h->g, tp, (float)(1.0 / h->alpha), (float)h->p, h->flags,
+                      (cudaStream_t)stream);
     SFSEG_LAUNCHED();
     return SFSEG_OK;
 }
@@ -389,8 +395,7 @@ int sfseg_rayleigh(sfseg_handle* h, const sfseg_neighborhood* nb, const float* x
     float* y = (float*)h->vbuf[0];
     double* a = h->scratch;
     SFSEG_CUDA(cudaMemsetAsync(a, 0, sizeof(double) * 4, s));
-    launch_apply(x, h->g.W, y, h->g.W, h->f32, h->g, tp, (float)(1.0 / h->alpha), (float)h->p, nullptr, nullptr,
-                 h->flags, s);
+    launch_apply_user(x, y, (float*)h->vbuf[1], h->f32, h->g, tp, (float)(1.0 / h->alpha), (float)h->p, h->flags, s);
     launch_dot2(x, y, h->N, a, s);
     launch_resid(x, y, h->N, a, s);
     SFSEG_LAUNCHED();

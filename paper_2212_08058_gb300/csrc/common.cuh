@@ -15,6 +15,7 @@ constexpr int kMaxRW = 8;
 constexpr int kFlagBadFeature = 1;   // a feature value was negative, NaN or Inf
 constexpr int kFlagZeroNorm = 2;     // an iterate norm was exactly zero
 constexpr int kFlagNonfinite = 4;    // an iterate norm was NaN or Inf
+constexpr int kFlagTimeout = 8;      // a bounded wait inside a kernel gave up
 
 // 1D factors of the separable Gaussian (Sec. 4.2), index d + r for offset d in [-r, r].
 struct Taps {

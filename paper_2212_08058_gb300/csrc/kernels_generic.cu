@@ -130,6 +130,10 @@ void launch_iterate(const void* vin, int vin_type, void* out, int out_type, bool
                     int f_type, float* ckpt, Geom g, const Taps& tp, float inv_alpha, float p,
                     const double* acc_in, double* acc_out, int* flags, cudaStream_t s) {
     using bf = __nv_bfloat16;
+    // The TMA kernel serves the method's radii; recording checkpoints uses the generic one.
+    if (ckpt == nullptr && fast_iterate_supported(tp) &&
+        launch_iterate_fast(vin, vin_type, out, out_type, out_x, f, g, tp, inv_alpha, p, acc_in, acc_out, flags, s))
+        return;
 #define SFSEG_IT(TVI, TVO, TF, OX) \
     iterate_t<TVI, TVO, TF, OX>(vin, out, f, ckpt, g, tp, inv_alpha, p, acc_in, acc_out, flags, s)
     // A step of the bf16 phase reads v and f in bf16 and writes bf16, or float32 when the next
@@ -160,6 +164,32 @@ void launch_apply(const float* x, int x_pitch, float* y, int y_pitch, const floa
     op.p = p;
     op.s = 1.f;
     run_stencil(op, tp, 16, acc_in, acc_out, nullptr, flags, s);
+}
+
+// v = u x from a caller-layout x into the internal layout (the state the iteration kernels read).
+__global__ void to_state_kernel(const float* x, const float* f32, float p, Geom g, float* v) {
+    const int64_t HW = (int64_t)g.H * g.W, N = HW * g.T;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = i / HW, rem = i - t * HW;
+        const int64_t h = rem / g.W, wc = rem - h * g.W;
+        const int64_t j = (t * g.H + h) * g.pitch + wc;
+        v[j] = unary_pow(f32[j], p) * x[i];
+    }
+}
+
+void launch_apply_user(const float* x, float* y, float* scratch_v, const float* f32, Geom g, const Taps& tp,
+                       float inv_alpha, float p, int* flags, cudaStream_t s) {
+    if (fast_iterate_supported(tp)) {
+        const int64_t N = (int64_t)g.T * g.H * g.W;
+        int blocks = (int)((N + 255) / 256);
+        if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
+        to_state_kernel<<<blocks, 256, 0, s>>>(x, f32, p, g, scratch_v);
+        count_launches(1);
+        // one unscaled step (no norm input) that writes x~ = A x into the caller's layout
+        if (launch_iterate_fast(scratch_v, kF32, y, kF32, true, f32, g, tp, inv_alpha, p, nullptr, nullptr, flags, s))
+            return;
+    }
+    launch_apply(x, g.W, y, g.W, f32, g, tp, inv_alpha, p, nullptr, nullptr, flags, s);
 }
 
 // -------------------------------------------------------------------------- Eq. 9 combine

@@ -31,6 +31,13 @@ void launch_iterate(const void* vin, int vin_type, void* out, int out_type, bool
                     float inv_alpha, float p, const double* acc_in, double* acc_out, int* flags,
                     cudaStream_t s);
 
+// TMA-staged step for the radii (1,3,3) and (2,7,7) (kernels_fast.cu).  Returns false when the
+// radius is not one of them or a tensor map cannot be encoded; nothing is launched then.
+bool fast_iterate_supported(const Taps& tp);
+bool launch_iterate_fast(const void* vin, int vin_type, void* out, int out_type, bool out_x, const void* f,
+                         const Geom& g, const Taps& tp, float inv_alpha, float p, const double* acc_in,
+                         double* acc_out, int* flags, cudaStream_t s);
+
 // y = s * A x in the plain (x-space) form: x with pitch x_pitch, y with pitch y_pitch, FP32
 // features; s = 1/sqrt(*acc_in) (or 1 if acc_in is null); acc_out += ||y||^2 (nullable).
 void launch_apply(const float* x, int x_pitch, float* y, int y_pitch, const float* f32, Geom g,
@@ -39,6 +46,11 @@ void launch_apply(const float* x, int x_pitch, float* y, int y_pitch, const floa
 
 // bf16 copy of a float32 array (n elements).
 void launch_to_bf16(const float* a, __nv_bfloat16* b, int64_t n, cudaStream_t s);
+
+// y = A x for caller-layout x and y (FP32); scratch_v holds one internal-layout volume.  Uses
+// the TMA kernel for the radii it serves, the generic stencil otherwise.
+void launch_apply_user(const float* x, float* y, float* scratch_v, const float* f32, Geom g, const Taps& tp,
+                       float inv_alpha, float p, int* flags, cudaStream_t s);
 
 // x *= 1/sqrt(*acc) over a caller-layout volume.
 void launch_scale_inv_norm(float* x, int64_t n, const double* acc, int* flags, cudaStream_t s);

@@ -1,0 +1,802 @@
+// net.cu -- the learned warm start: a 4-layer 3x3x3 convolutional network that predicts a
+// start vector x0 >= 0 for the power iteration from the raw input channels.  (The paper starts
+// from a uniform vector or from S_m, Alg. 1 line 3; this network is the BASELINE addition.)
+//
+//   L1: C_in (<= 16, zero-padded to 16) -> 32, ReLU      L2, L3: 32 -> 32, ReLU
+//   L4: 32 -> 1 (computed as 16 output channels, only the first non-zero), softplus
+//
+// Activations are bf16 in channels-last layout [T][H][W][C]; every convolution is an implicit
+// GEMM on the 5th-generation tensor cores (tcgen05.mma, kind::f16, bf16 x bf16 -> fp32 in TMEM):
+//   D[v, co] = sum_{tap, ci} X[v + tap, ci] W[co, tap, ci],   M = 128 voxels of one row along w,
+//   N = output channels, K = 16 input channels per instruction, 27 taps x C_in/16 instructions.
+// The A operand is read straight from a TMA-filled ring of input rows in the canonical
+// no-swizzle K-major layout ([8-channel chunk][3 frames][130 voxels][8 channels]); a tap's shift
+// along w is a 16-byte offset of the descriptor's start address, along t a 2080-byte offset,
+// along h another ring slot.  All weights of the layer stay in shared memory.  One warp issues
+// the TMA copies, one the MMAs, four read the accumulator from TMEM (double-buffered) and run
+// the epilogue.  The backward pass reuses the same kernel for the data gradient (flipped taps,
+// transposed channels, ReLU mask in the epilogue); the weight gradient is a reduction over
+// voxels on the CUDA cores.
+#include <cuda.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/sfseg.h"
+#include "common.cuh"
+#include "launch.h"
+
+namespace sfseg {
+namespace net {
+
+constexpr int MT = 128;                 // voxels per MMA tile (rows of A)
+constexpr int RW = MT + 2;              // voxels per loaded row (w halo of 1)
+constexpr int CHUNK_DATA = 3 * RW * 16;    // one 8-channel chunk of 3 frames: 6240 B
+constexpr int CHUNK_BYTES = (CHUNK_DATA + 127) / 128 * 128;   // its stride (128-byte aligned TMA target)
+constexpr int NSLOT = 4;                // input-row ring
+constexpr int NTHR = 192;               // 6 warps
+constexpr int HR = 32;                  // output rows per CTA
+constexpr long long kSpin = 1ll << 26;
+
+enum Epi { EPI_RELU = 0, EPI_LAST = 1, EPI_MASK = 2 };
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mb_init(uint64_t* b, uint32_t n) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void mb_expect(uint64_t* b, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mb_arrive(uint64_t* b) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
+}
+__device__ __forceinline__ bool mb_try(uint64_t* b, uint32_t par) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(par)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: on timeout raise the flag and report failure (the caller then stops issuing).
+__device__ __forceinline__ bool mb_wait(uint64_t* b, uint32_t par, int* flags) {
+    for (long long i = 0; i < kSpin; ++i)
+        if (mb_try(b, par)) return true;
+    atomicOr(flags, kFlagTimeout);
+    return false;
+}
+__device__ __forceinline__ void tma4(void* dst, const CUtensorMap* m, uint64_t* b, int c0, int c1, int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(su32(dst)), "l"(m), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(su32(b))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(su32(dst)), "l"(src), "r"(bytes), "r"(su32(b))
+                 : "memory");
+}
+// Shared-memory matrix descriptor: canonical K-major layout without swizzle.
+__device__ __forceinline__ uint64_t sdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+// Instruction descriptor, kind::f16: bf16 A and B (K-major), fp32 D, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(MT >> 4) << 24);
+}
+__device__ __forceinline__ void umma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+        ::"r"(d), "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+__device__ __forceinline__ void umma_commit(uint64_t* b) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, uint32_t (&r)[N]);
+template <>
+__device__ __forceinline__ void tmem_ld<32>(uint32_t t, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(t));
+}
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t t, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(t));
+}
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+struct ConvArgs {
+    int T, H, W;
+    const __nv_bfloat16* wpack;   // packed weights (layout of the smem B operand)
+    const float* bias;            // [COUT] or null
+    void* out;                    // EPI_RELU/EPI_MASK: bf16 [T][H][W][COUT]; EPI_LAST: float z [T][H][W]
+    float* out2;                  // EPI_LAST: x0 = softplus(z) [T][H][W]
+    const __nv_bfloat16* mask;    // EPI_MASK: activation [T][H][W][COUT] whose sign gates the output
+    int* flags;
+};
+
+template <int CIN, int COUT>
+struct ConvCfg {
+    static constexpr int NCH = CIN / 8;                       // 8-channel chunks of A
+    static constexpr int KS = CIN / 16;                       // MMAs per tap
+    static constexpr int SLOT_BYTES = NCH * CHUNK_BYTES;
+    static constexpr int WBYTES = 27 * KS * 2 * COUT * 16;    // packed weights
+    static constexpr int SMEM = WBYTES + NSLOT * SLOT_BYTES + 16 * 8 + 16 + 128;
+    static constexpr int TMEM_COLS = COUT <= 16 ? 32 : 64;    // two accumulator buffers
+};
+
+template <int CIN, int COUT, int EPI>
+__global__ void __launch_bounds__(NTHR, 1)
+conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
+    using C = ConvCfg<CIN, COUT>;
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    unsigned char* sm = (unsigned char*)(((uintptr_t)sm_raw + 127) & ~(uintptr_t)127);
+    unsigned char* wsm = sm;                                   // weights
+    unsigned char* ring = sm + C::WBYTES;                      // NSLOT input rows
+    uint64_t* bar = reinterpret_cast<uint64_t*>(ring + NSLOT * C::SLOT_BYTES);
+    uint64_t* full = bar;            // [NSLOT]
+    uint64_t* empty = bar + 4;       // [NSLOT]
+    uint64_t* accf = bar + 8;        // [2]
+    uint64_t* acce = bar + 10;       // [2]
+    uint64_t* wbar = bar + 12;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 16);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // work item: (t, w segment, row range)
+    const int nws = (a.W + MT - 1) / MT, nhr = (a.H + HR - 1) / HR;
+    int item = blockIdx.x;
+    const int hr = item % nhr;
+    item /= nhr;
+    const int ws = item % nws;
+    const int t = item / nws;
+    const int w0 = ws * MT, hs = hr * HR, he = min(a.H, hs + HR);
+    const int nout = he - hs, nin = nout + 2;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < 4; ++i) {
+            mb_init(&full[i], 1);
+            mb_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mb_init(&accf[i], 1);
+            mb_init(&acce[i], 4);
+        }
+        mb_init(wbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(C::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {   // ---------------- producer: weights, then the input rows
+            mb_expect(wbar, C::WBYTES);
+            bulk_g2s(wsm, a.wpack, C::WBYTES, wbar);
+            for (int i = 0; i < nin; ++i) {
+                const int s = i % NSLOT;
+                if (i >= NSLOT && !mb_wait(&empty[s], (uint32_t)((i / NSLOT - 1) & 1), a.flags)) break;
+                mb_expect(&full[s], C::NCH * CHUNK_DATA);
+                unsigned char* dst = ring + s * C::SLOT_BYTES;
+                for (int k = 0; k < C::NCH; ++k) tma4(dst + k * CHUNK_BYTES, &xin, &full[s], 8 * k, w0 - 1, hs - 1 + i, t - 1);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // ---------------- MMA issuer
+            bool ok = mb_wait(wbar, 0, a.flags);
+            const uint32_t id = idesc_bf16(COUT);
+            const uint32_t wbase = su32(wsm), rbase = su32(ring);
+            for (int j = 0; ok && j < nout; ++j) {
+                if (j == 0) ok = mb_wait(&full[0], 0, a.flags) && mb_wait(&full[1], 0, a.flags);
+                ok = ok && mb_wait(&full[(j + 2) % NSLOT], (uint32_t)(((j + 2) / NSLOT) & 1), a.flags);
+                const int b = j & 1;
+                if (ok && j >= 2) ok = mb_wait(&acce[b], (uint32_t)((j / 2 - 1) & 1), a.flags);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * (C::TMEM_COLS / 2));
+                uint32_t accum = 0;
+#pragma unroll 1
+                for (int dh = 0; dh < 3; ++dh) {
+                    const uint32_t slot = rbase + (uint32_t)(((j + dh) % NSLOT) * C::SLOT_BYTES);
+#pragma unroll
+                    for (int dt = 0; dt < 3; ++dt)
+#pragma unroll
+                        for (int dw = 0; dw < 3; ++dw) {
+                            const int tap = (dt * 3 + dh) * 3 + dw;
+#pragma unroll
+                            for (int ks = 0; ks < C::KS; ++ks) {
+                                const uint64_t ad = sdesc(slot + (uint32_t)(2 * ks * CHUNK_BYTES + dt * RW * 16 + dw * 16),
+                                                          CHUNK_BYTES, 128);
+                                const uint64_t bd = sdesc(wbase + (uint32_t)((tap * C::KS + ks) * 2 * COUT * 16),
+                                                          COUT * 16, 128);
+                                umma(d, ad, bd, id, accum);
+                                accum = 1;
+                            }
+                        }
+                }
+                umma_commit(&accf[b]);
+                umma_commit(&empty[j % NSLOT]);
+            }
+        }
+    } else {   // ---------------- epilogue: warps 2..5
+        const int q = warp & 3;          // TMEM lane quadrant of this warp
+        const int v = q * 32 + lane;     // voxel within the tile
+        const int w = w0 + v;
+        for (int j = 0; j < nout; ++j) {
+            const int b = j & 1;
+            const bool ok = mb_wait(&accf[b], (uint32_t)((j / 2) & 1), a.flags);
+            tc_fence_after();
+            uint32_t r[COUT];
+            tmem_ld<COUT>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * (C::TMEM_COLS / 2)), r);
+            tmem_ld_wait();
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mb_arrive(&acce[b]);
+            if (!ok) break;
+            const int h = hs + j;
+            if (w >= a.W) continue;
+            const int64_t vox = ((int64_t)t * a.H + h) * a.W + w;
+            if constexpr (EPI == EPI_LAST) {
+                const float z = __uint_as_float(r[0]) + a.bias[0];
+                reinterpret_cast<float*>(a.out)[vox] = z;
+                a.out2[vox] = z > 20.f ? z : log1pf(expf(z));   // softplus
+            } else {
+                __nv_bfloat162 o[COUT / 2];
+                if constexpr (EPI == EPI_RELU) {
+#pragma unroll
+                    for (int c = 0; c < COUT / 2; ++c) {
+                        const float x0 = fmaxf(__uint_as_float(r[2 * c]) + a.bias[2 * c], 0.f);
+                        const float x1 = fmaxf(__uint_as_float(r[2 * c + 1]) + a.bias[2 * c + 1], 0.f);
+                        o[c] = __floats2bfloat162_rn(x0, x1);
+                    }
+                } else {   // EPI_MASK: dL/dz of the layer below = dL/da * [a > 0]
+                    const uint4* mp = reinterpret_cast<const uint4*>(a.mask + vox * COUT);
+#pragma unroll
+                    for (int c4 = 0; c4 < COUT / 8; ++c4) {
+                        const uint4 m4 = mp[c4];
+                        const __nv_bfloat162* mm = reinterpret_cast<const __nv_bfloat162*>(&m4);
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const float2 mf = __bfloat1622float2(mm[e]);
+                            const int c = c4 * 4 + e;
+                            o[c] = __floats2bfloat162_rn(mf.x > 0.f ? __uint_as_float(r[2 * c]) : 0.f,
+                                                         mf.y > 0.f ? __uint_as_float(r[2 * c + 1]) : 0.f);
+                        }
+                    }
+                }
+                uint4* op = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(a.out) + vox * COUT);
+#pragma unroll
+                for (int c4 = 0; c4 < COUT / 8; ++c4) op[c4] = reinterpret_cast<const uint4*>(o)[c4];
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
+}
+
+// ------------------------------------------------------------------------ small kernels
+// Caller's channels [C][T][H][W] (float or bf16) -> bf16 [T][H][W][16], channels >= C zero.
+template <typename TIn>
+__global__ void to_channels_last(const TIn* f, int C, int64_t N, __nv_bfloat16* out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        __nv_bfloat16 v[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(c < C ? ldf(f + (int64_t)c * N + i) : 0.f);
+        uint4* o = reinterpret_cast<uint4*>(out + i * 16);
+        o[0] = reinterpret_cast<const uint4*>(v)[0];
+        o[1] = reinterpret_cast<const uint4*>(v)[1];
+    }
+}
+
+// Pack fp32 weights W[co][27][ci] (co < cout, ci < cin) into the B-operand layout
+// [tap][ks][chunk(2)][COUTP][8] bf16 with zero padding to COUTP x CINP; `flip` packs the
+// data-gradient kernel instead: W'[ci][tap][co] = W[co][26 - tap][ci].
+__global__ void pack_weights(const float* W, int cout, int cin, int COUTP, int CINP, int flip, __nv_bfloat16* out) {
+    const int KS = CINP / 16;
+    const int total = 27 * KS * 2 * COUTP * 8;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total; idx += gridDim.x * blockDim.x) {
+        int r = idx;
+        const int e = r % 8; r /= 8;
+        const int n = r % COUTP; r /= COUTP;
+        const int ch = r % 2; r /= 2;
+        const int ks = r % KS; r /= KS;
+        const int tap = r;
+        const int k = ks * 16 + ch * 8 + e;     // input-channel index of the packed conv
+        float v = 0.f;
+        if (!flip) {
+            if (n < cout && k < cin) v = W[((int64_t)n * 27 + tap) * cin + k];
+        } else {   // packed conv: out channel n = ci of W, in channel k = co of W
+            if (n < cin && k < cout) v = W[((int64_t)k * 27 + (26 - tap)) * cin + n];
+        }
+        out[idx] = __float2bfloat16_rn(v);
+    }
+}
+
+// Weight gradient on the CUDA cores: dW[co][tap][ci] += sum_v dz[v][co] * x[v + tap][ci],
+// db[co] += sum_v dz[v][co].  dz: bf16 [N][dzc], x: bf16 [N][xc]; grid (27, splits).
+__global__ void wgrad_kernel(const __nv_bfloat16* dz, int dzc, int cout, const __nv_bfloat16* x, int xc, int cin, int T,
+                             int H, int W, float* dW, float* db) {
+    const int tap = blockIdx.x;
+    const int dt = tap / 9 - 1, dh = (tap / 3) % 3 - 1, dw = tap % 3 - 1;
+    const int64_t N = (int64_t)T * H * W;
+    const int nsplit = gridDim.y;
+    const int64_t per = (N + nsplit - 1) / nsplit;
+    const int64_t v0 = blockIdx.y * per, v1 = min(N, v0 + per);
+    __shared__ float sdz[64][33];
+    __shared__ float sx[64][33];
+    const int co = threadIdx.x / 32, ci = threadIdx.x % 32;   // 1024 threads: (co, ci)
+    float acc = 0.f, accb = 0.f;
+    for (int64_t base = v0; base < v1; base += 64) {
+        for (int i = threadIdx.x; i < 64 * 32; i += blockDim.x) {
+            const int vv = i / 32, c = i % 32;
+            const int64_t v = base + vv;
+            float a = 0.f, bx = 0.f;
+            if (v < v1) {
+                if (c < cout) a = __bfloat162float(dz[v * dzc + c]);
+                const int64_t t = v / ((int64_t)H * W), rem = v % ((int64_t)H * W);
+                const int h = (int)(rem / W), w = (int)(rem % W);
+                const int tt = (int)t + dt, hh = h + dh, ww = w + dw;
+                if (c < cin && tt >= 0 && tt < T && hh >= 0 && hh < H && ww >= 0 && ww < W)
+                    bx = __bfloat162float(x[(((int64_t)tt * H + hh) * W + ww) * xc + c]);
+            }
+            sdz[vv][c] = a;
+            sx[vv][c] = bx;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int vv = 0; vv < 64; ++vv) {
+            acc = fmaf(sdz[vv][co], sx[vv][ci], acc);
+            accb += sdz[vv][co];
+        }
+        __syncthreads();
+    }
+    if (co < cout && ci < cin) atomicAdd(&dW[((int64_t)co * 27 + tap) * cin + ci], acc);
+    if (tap == 0 && ci == 0 && co < cout) atomicAdd(&db[co], accb);
+}
+
+// Cosine-loss pieces: sums of x*g, x*x, g*g (FP64 via block sums).
+__global__ void cos_sums(const float* x, const float* g, int64_t n, double* acc) {
+    float a = 0.f, b = 0.f, c = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        a += x[i] * g[i];
+        b += x[i] * x[i];
+        c += g[i] * g[i];
+    }
+    double s = block_sum((double)a);
+    if (threadIdx.x == 0) atomicAdd(acc, s);
+    s = block_sum((double)b);
+    if (threadIdx.x == 0) atomicAdd(acc + 1, s);
+    s = block_sum((double)c);
+    if (threadIdx.x == 0) atomicAdd(acc + 2, s);
+}
+
+// dL/dz4 for L = 1 - <x,g>/(|x||g|), x = softplus(z4): written as channel 0 of a 16-channel bf16
+// tensor (the input of the last layer's data-gradient convolution), other channels zero.
+__global__ void cos_grad(const float* x, const float* g, const float* z, int64_t n, const double* acc,
+                         __nv_bfloat16* dz16) {
+    const double xg = acc[0], xx = acc[1], gg = acc[2];
+    const double nx = sqrt(xx), ng = sqrt(gg);
+    const float c1 = (float)(1.0 / (nx * ng)), c2 = (float)(xg / (nx * ng) / xx);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float dx = -(g[i] * c1 - x[i] * c2);
+        const float sg = 1.f / (1.f + expf(-z[i]));
+        __nv_bfloat16 v[16];
+        v[0] = __float2bfloat16_rn(dx * sg);
+#pragma unroll
+        for (int c = 1; c < 16; ++c) v[c] = __float2bfloat16_rn(0.f);
+        uint4* o = reinterpret_cast<uint4*>(dz16 + i * 16);
+        o[0] = reinterpret_cast<const uint4*>(v)[0];
+        o[1] = reinterpret_cast<const uint4*>(v)[1];
+    }
+}
+
+// AdamW (decoupled weight decay) on fp32 parameters.
+__global__ void adamw_kernel(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2,
+                             float eps, float wd, float bc1, float bc2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * ((mi / bc1) / (sqrtf(vi / bc2) + eps) + wd * p[i]);
+    }
+}
+
+}  // namespace net
+}  // namespace sfseg
+
+// ================================================================================ host side
+using namespace sfseg;
+using namespace sfseg::net;
+
+namespace {
+
+typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                             const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                             CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn encode() {
+    static EncodeFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeFn)p;
+    }
+    return fn;
+}
+
+// 4D map over a channels-last bf16 activation [T][H][W][C]; box = 8 channels x 130 voxels x
+// 1 row x 3 frames (one A chunk of one input row).
+bool act_map(CUtensorMap* m, const void* base, int C, int T, int H, int W) {
+    EncodeFn fn = encode();
+    if (!fn) return false;
+    cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)T};
+    cuuint64_t str[3] = {(cuuint64_t)C * 2, (cuuint64_t)C * 2 * W, (cuuint64_t)C * 2 * W * H};
+    cuuint32_t box[4] = {8, (cuuint32_t)RW, 1, 3};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, str, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+int blocks_for(int64_t n, int per = 256) {
+    int64_t b = (n + per - 1) / per;
+    const int cap = 16 * num_sms();
+    return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+}  // namespace
+
+struct sfseg_net {
+    int cin = 8;
+    int64_t off[8] = {0};     // W1 b1 W2 b2 W3 b3 W4 b4
+    int64_t np = 0;
+    float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+    int64_t step = 0;
+    bool packed = false;
+    __nv_bfloat16* wf[4] = {nullptr, nullptr, nullptr, nullptr};   // forward packs
+    __nv_bfloat16* wb[4] = {nullptr, nullptr, nullptr, nullptr};   // data-gradient packs (layers 2..4)
+    int64_t cap = 0;
+    __nv_bfloat16 *x16 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *dz16 = nullptr, *dza = nullptr,
+                  *dzb = nullptr;
+    float *z4 = nullptr, *x0 = nullptr;
+    double* acc = nullptr;
+    int* flags = nullptr;
+    bool have_fwd = false;
+};
+
+namespace {
+
+int nfail(int code, const std::string& m) { return set_last_error(code, m.c_str()); }
+
+#define NET_CUDA(call)                                                                                  \
+    do {                                                                                                \
+        cudaError_t e_ = (call);                                                                        \
+        if (e_ != cudaSuccess)                                                                          \
+            return nfail(e_ == cudaErrorMemoryAllocation ? SFSEG_ERR_OOM : SFSEG_ERR_CUDA,              \
+                         std::string(#call) + ": " + cudaGetErrorString(e_));                           \
+    } while (0)
+
+const int kCout[4] = {32, 32, 32, 1};
+
+int layer_cin(const sfseg_net* n, int l) { return l == 0 ? n->cin : 32; }
+
+// Forward buffers (x16, a1, a2, z4, x0) always; a3 and the gradient buffers only for training.
+// Inference writes layer 3's output over layer 1's (layer 3 reads a2, so a1 is free by then):
+// 168 bytes per voxel instead of 392.
+int ensure_ws(sfseg_net* n, int64_t N, bool train) {
+    if (n->cap < N) {
+        cudaFree(n->x16); cudaFree(n->a1); cudaFree(n->a2); cudaFree(n->a3);
+        cudaFree(n->dz16); cudaFree(n->dza); cudaFree(n->dzb); cudaFree(n->z4); cudaFree(n->x0);
+        n->x16 = n->a1 = n->a2 = n->a3 = n->dz16 = n->dza = n->dzb = nullptr;
+        n->z4 = n->x0 = nullptr;
+        n->cap = 0;
+        NET_CUDA(cudaMalloc(&n->x16, N * 16 * 2));
+        NET_CUDA(cudaMalloc(&n->a1, N * 32 * 2));
+        NET_CUDA(cudaMalloc(&n->a2, N * 32 * 2));
+        NET_CUDA(cudaMalloc(&n->z4, N * 4));
+        NET_CUDA(cudaMalloc(&n->x0, N * 4));
+        n->cap = N;
+    }
+    if (train && !n->dz16) {
+        NET_CUDA(cudaMalloc(&n->a3, n->cap * 32 * 2));
+        NET_CUDA(cudaMalloc(&n->dz16, n->cap * 16 * 2));
+        NET_CUDA(cudaMalloc(&n->dza, n->cap * 32 * 2));
+        NET_CUDA(cudaMalloc(&n->dzb, n->cap * 32 * 2));
+    }
+    return SFSEG_OK;
+}
+
+template <int CIN, int COUT, int EPI>
+int run_conv(const void* in, int T, int H, int W, const __nv_bfloat16* wpack, const float* bias, void* out,
+             float* out2, const __nv_bfloat16* mask, int* flags, cudaStream_t s) {
+    using Cf = ConvCfg<CIN, COUT>;
+    CUtensorMap m;
+    if (!act_map(&m, in, CIN, T, H, W)) return nfail(SFSEG_ERR_CUDA, "tensor map encoding failed");
+    auto k = conv3d_tc<CIN, COUT, EPI>;
+    static bool attr = false;
+    if (!attr) {
+        NET_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM));
+        attr = true;
+    }
+    ConvArgs a;
+    a.T = T; a.H = H; a.W = W;
+    a.wpack = wpack; a.bias = bias; a.out = out; a.out2 = out2; a.mask = mask; a.flags = flags;
+    const int items = T * ((W + MT - 1) / MT) * ((H + HR - 1) / HR);
+    k<<<items, NTHR, Cf::SMEM, s>>>(m, a);
+    count_launches(1);
+    NET_CUDA(cudaGetLastError());
+    return SFSEG_OK;
+}
+
+int pack_all(sfseg_net* n, cudaStream_t s) {
+    if (n->packed) return SFSEG_OK;
+    const int cinp[4] = {16, 32, 32, 32}, coutp[4] = {32, 32, 32, 16};
+    for (int l = 0; l < 4; ++l) {
+        const int total = 27 * (cinp[l] / 16) * 2 * coutp[l] * 8;
+        pack_weights<<<(total + 255) / 256, 256, 0, s>>>(n->p + n->off[2 * l], kCout[l], layer_cin(n, l), coutp[l],
+                                                         cinp[l], 0, n->wf[l]);
+        count_launches(1);
+        if (l > 0) {   // data gradient of layer l: input = dz of its output (COUT_l channels, padded)
+            const int ci2 = l == 3 ? 16 : 32;
+            const int tot2 = 27 * (ci2 / 16) * 2 * 32 * 8;
+            pack_weights<<<(tot2 + 255) / 256, 256, 0, s>>>(n->p + n->off[2 * l], kCout[l], 32, 32, ci2, 1, n->wb[l]);
+            count_launches(1);
+        }
+    }
+    NET_CUDA(cudaGetLastError());
+    n->packed = true;
+    return SFSEG_OK;
+}
+
+int check_flags(sfseg_net* n, cudaStream_t s) {
+    int fl = 0;
+    NET_CUDA(cudaMemcpyAsync(&fl, n->flags, sizeof(int), cudaMemcpyDeviceToHost, s));
+    NET_CUDA(cudaStreamSynchronize(s));
+    if (fl) {
+        NET_CUDA(cudaMemsetAsync(n->flags, 0, sizeof(int), s));
+        return nfail(SFSEG_ERR_TIMEOUT, "a bounded wait inside the convolution kernel gave up");
+    }
+    return SFSEG_OK;
+}
+
+int net_forward(sfseg_net* n, const void* feats, int dtype, int C, int T, int H, int W, bool train, cudaStream_t s) {
+    const int64_t N = (int64_t)T * H * W;
+    if (int rc = ensure_ws(n, N, train)) return rc;
+    __nv_bfloat16* a3 = train ? n->a3 : n->a1;   // inference: layer 3 overwrites layer 1's output
+    if (int rc = pack_all(n, s)) return rc;
+    if (dtype == SFSEG_F32)
+        to_channels_last<float><<<blocks_for(N), 256, 0, s>>>((const float*)feats, C, N, n->x16);
+    else
+        to_channels_last<__nv_bfloat16><<<blocks_for(N), 256, 0, s>>>((const __nv_bfloat16*)feats, C, N, n->x16);
+    count_launches(1);
+    if (int rc = run_conv<16, 32, EPI_RELU>(n->x16, T, H, W, n->wf[0], n->p + n->off[1], n->a1, nullptr, nullptr,
+                                            n->flags, s))
+        return rc;
+    if (int rc = run_conv<32, 32, EPI_RELU>(n->a1, T, H, W, n->wf[1], n->p + n->off[3], n->a2, nullptr, nullptr,
+                                            n->flags, s))
+        return rc;
+    if (int rc = run_conv<32, 32, EPI_RELU>(n->a2, T, H, W, n->wf[2], n->p + n->off[5], a3, nullptr, nullptr,
+                                            n->flags, s))
+        return rc;
+    if (int rc = run_conv<32, 16, EPI_LAST>(a3, T, H, W, n->wf[3], n->p + n->off[7], n->z4, n->x0, nullptr,
+                                            n->flags, s))
+        return rc;
+    n->have_fwd = true;
+    return SFSEG_OK;
+}
+
+int wgrad(sfseg_net* n, int l, const __nv_bfloat16* dz, int dzc, const __nv_bfloat16* x, int xc, int T, int H, int W,
+          cudaStream_t s) {
+    const int64_t N = (int64_t)T * H * W;
+    int splits = (int)((N + 4095) / 4096);
+    if (splits > 24) splits = 24;
+    if (splits < 1) splits = 1;
+    wgrad_kernel<<<dim3(27, splits), 1024, 0, s>>>(dz, dzc, kCout[l], x, xc, layer_cin(n, l), T, H, W,
+                                                   n->g + n->off[2 * l], n->g + n->off[2 * l + 1]);
+    count_launches(1);
+    NET_CUDA(cudaGetLastError());
+    return SFSEG_OK;
+}
+
+uint64_t splitmix(uint64_t& x) {
+    uint64_t z = (x += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+int check_vol(int C, int T, int H, int W, const void* feats) {
+    if (!feats) return nfail(SFSEG_ERR_INVALID_ARG, "null features");
+    if (C < 1 || C > 16) return nfail(SFSEG_ERR_INVALID_ARG, "the network takes 1..16 channels");
+    if (T < 1 || H < 1 || W < 1) return nfail(SFSEG_ERR_SHAPE, "empty volume");
+    if ((int64_t)T * H * W >= (int64_t(1) << 31)) return nfail(SFSEG_ERR_SHAPE, "volume too large");
+    return SFSEG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sfseg_net_create(int c_in, uint64_t seed, sfseg_net** out) {
+    if (!out) return nfail(SFSEG_ERR_INVALID_ARG, "null out");
+    *out = nullptr;
+    if (c_in < 1 || c_in > 16) return nfail(SFSEG_ERR_INVALID_ARG, "c_in must be in [1, 16]");
+    sfseg_net* n = new sfseg_net();
+    n->cin = c_in;
+    int64_t o = 0;
+    for (int l = 0; l < 4; ++l) {
+        n->off[2 * l] = o;
+        o += (int64_t)kCout[l] * 27 * layer_cin(n, l);
+        n->off[2 * l + 1] = o;
+        o += kCout[l];
+    }
+    n->np = o;
+    // He-normal weights (Box-Muller on a splitmix64 stream), zero biases.
+    std::vector<float> h((size_t)o, 0.f);
+    uint64_t st = seed;
+    for (int l = 0; l < 4; ++l) {
+        const double sd = std::sqrt(2.0 / (27.0 * layer_cin(n, l)));
+        for (int64_t i = n->off[2 * l]; i < n->off[2 * l + 1]; ++i) {
+            const double u1 = ((splitmix(st) >> 11) + 1.0) / 9007199254740993.0;
+            const double u2 = (splitmix(st) >> 11) / 9007199254740992.0;
+            h[(size_t)i] = (float)(sd * std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2));
+        }
+    }
+    const int cinp[4] = {16, 32, 32, 32}, coutp[4] = {32, 32, 32, 16};
+    cudaError_t e = cudaSuccess;
+    auto al = [&](void** p, size_t bytes) { if (e == cudaSuccess) e = cudaMalloc(p, bytes); };
+    al((void**)&n->p, o * 4);
+    al((void**)&n->g, o * 4);
+    al((void**)&n->m, o * 4);
+    al((void**)&n->v, o * 4);
+    for (int l = 0; l < 4; ++l) al((void**)&n->wf[l], (size_t)27 * (cinp[l] / 16) * 2 * coutp[l] * 8 * 2);
+    for (int l = 1; l < 4; ++l) al((void**)&n->wb[l], (size_t)27 * ((l == 3 ? 16 : 32) / 16) * 2 * 32 * 8 * 2);
+    al((void**)&n->acc, 8 * sizeof(double));
+    al((void**)&n->flags, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpy(n->p, h.data(), o * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(n->m, 0, o * 4);
+    if (e == cudaSuccess) e = cudaMemset(n->v, 0, o * 4);
+    if (e == cudaSuccess) e = cudaMemset(n->flags, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        sfseg_net_destroy(n);
+        return nfail(e == cudaErrorMemoryAllocation ? SFSEG_ERR_OOM : SFSEG_ERR_CUDA,
+                     std::string("sfseg_net_create: ") + cudaGetErrorString(e));
+    }
+    *out = n;
+    return SFSEG_OK;
+}
+
+int sfseg_net_destroy(sfseg_net* n) {
+    if (!n) return SFSEG_OK;
+    cudaDeviceSynchronize();
+    cudaFree(n->p); cudaFree(n->g); cudaFree(n->m); cudaFree(n->v);
+    for (int l = 0; l < 4; ++l) { cudaFree(n->wf[l]); cudaFree(n->wb[l]); }
+    cudaFree(n->x16); cudaFree(n->a1); cudaFree(n->a2); cudaFree(n->a3);
+    cudaFree(n->dz16); cudaFree(n->dza); cudaFree(n->dzb); cudaFree(n->z4); cudaFree(n->x0);
+    cudaFree(n->acc); cudaFree(n->flags);
+    delete n;
+    return SFSEG_OK;
+}
+
+int sfseg_net_num_params(sfseg_net* n, int64_t* count) {
+    if (!n || !count) return nfail(SFSEG_ERR_INVALID_ARG, "null argument");
+    *count = n->np;
+    return SFSEG_OK;
+}
+
+int sfseg_net_get_params(sfseg_net* n, float* host, int64_t count) {
+    if (!n || !host) return nfail(SFSEG_ERR_INVALID_ARG, "null argument");
+    if (count != n->np) return nfail(SFSEG_ERR_SHAPE, "parameter count mismatch");
+    NET_CUDA(cudaMemcpy(host, n->p, n->np * 4, cudaMemcpyDeviceToHost));
+    return SFSEG_OK;
+}
+
+int sfseg_net_set_params(sfseg_net* n, const float* host, int64_t count) {
+    if (!n || !host) return nfail(SFSEG_ERR_INVALID_ARG, "null argument");
+    if (count != n->np) return nfail(SFSEG_ERR_SHAPE, "parameter count mismatch");
+    NET_CUDA(cudaMemcpy(n->p, host, n->np * 4, cudaMemcpyHostToDevice));
+    n->packed = false;
+    return SFSEG_OK;
+}
+
+int sfseg_net_forward(sfseg_net* n, const void* features, int dtype, int C, int T, int H, int W, float* x0_out,
+                      void* stream) {
+    if (!n || !x0_out) return nfail(SFSEG_ERR_INVALID_ARG, "null argument");
+    if (int rc = check_vol(C, T, H, W, features)) return rc;
+    if (dtype != SFSEG_F32 && dtype != SFSEG_BF16) return nfail(SFSEG_ERR_DTYPE, "dtype must be F32 or BF16");
+    if (C > n->cin) return nfail(SFSEG_ERR_SHAPE, "more channels than the network was built for");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (int rc = net_forward(n, features, dtype, C, T, H, W, false, s)) return rc;
+    NET_CUDA(cudaMemcpyAsync(x0_out, n->x0, (size_t)T * H * W * 4, cudaMemcpyDeviceToDevice, s));
+    return SFSEG_OK;
+}
+
+int sfseg_net_backward(sfseg_net* n, const void* features, int dtype, int C, int T, int H, int W, const float* target,
+                       double* loss, float* grads_out, void* stream) {
+    if (!n || !target || !loss) return nfail(SFSEG_ERR_INVALID_ARG, "null argument");
+    if (int rc = check_vol(C, T, H, W, features)) return rc;
+    if (dtype != SFSEG_F32 && dtype != SFSEG_BF16) return nfail(SFSEG_ERR_DTYPE, "dtype must be F32 or BF16");
+    if (C > n->cin) return nfail(SFSEG_ERR_SHAPE, "more channels than the network was built for");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t N = (int64_t)T * H * W;
+    if (int rc = net_forward(n, features, dtype, C, T, H, W, true, s)) return rc;
+    NET_CUDA(cudaMemsetAsync(n->acc, 0, 8 * sizeof(double), s));
+    NET_CUDA(cudaMemsetAsync(n->g, 0, n->np * 4, s));
+    cos_sums<<<blocks_for(N), 256, 0, s>>>(n->x0, target, N, n->acc);
+    cos_grad<<<blocks_for(N), 256, 0, s>>>(n->x0, target, n->z4, N, n->acc, n->dz16);
+    count_launches(2);
+    // layer 4
+    if (int rc = wgrad(n, 3, n->dz16, 16, n->a3, 32, T, H, W, s)) return rc;
+    if (int rc = run_conv<16, 32, EPI_MASK>(n->dz16, T, H, W, n->wb[3], nullptr, n->dza, nullptr, n->a3, n->flags, s))
+        return rc;
+    // layer 3
+    if (int rc = wgrad(n, 2, n->dza, 32, n->a2, 32, T, H, W, s)) return rc;
+    if (int rc = run_conv<32, 32, EPI_MASK>(n->dza, T, H, W, n->wb[2], nullptr, n->dzb, nullptr, n->a2, n->flags, s))
+        return rc;
+    // layer 2
+    if (int rc = wgrad(n, 1, n->dzb, 32, n->a1, 32, T, H, W, s)) return rc;
+    if (int rc = run_conv<32, 32, EPI_MASK>(n->dzb, T, H, W, n->wb[1], nullptr, n->dza, nullptr, n->a1, n->flags, s))
+        return rc;
+    // layer 1
+    if (int rc = wgrad(n, 0, n->dza, 32, n->x16, 16, T, H, W, s)) return rc;
+    double a[3];
+    NET_CUDA(cudaMemcpyAsync(a, n->acc, sizeof(a), cudaMemcpyDeviceToHost, s));
+    if (int rc = check_flags(n, s)) return rc;
+    *loss = 1.0 - a[0] / std::sqrt(a[1] * a[2]);
+    if (grads_out) NET_CUDA(cudaMemcpy(grads_out, n->g, n->np * 4, cudaMemcpyDeviceToHost));
+    return SFSEG_OK;
+}
+
+int sfseg_net_adamw(sfseg_net* n, float lr, float beta1, float beta2, float eps, float weight_decay, void* stream) {
+    if (!n) return nfail(SFSEG_ERR_INVALID_ARG, "null net");
+    if (!(lr >= 0.f) || !(beta1 >= 0.f && beta1 < 1.f) || !(beta2 >= 0.f && beta2 < 1.f) || !(eps > 0.f))
+        return nfail(SFSEG_ERR_INVALID_ARG, "bad AdamW hyper-parameters");
+    cudaStream_t s = (cudaStream_t)stream;
+    n->step += 1;
+    const float bc1 = 1.f - std::pow(beta1, (float)n->step), bc2 = 1.f - std::pow(beta2, (float)n->step);
+    adamw_kernel<<<blocks_for(n->np), 256, 0, s>>>(n->p, n->g, n->m, n->v, n->np, lr, beta1, beta2, eps, weight_decay,
+                                                   bc1, bc2);
+    count_launches(1);
+    NET_CUDA(cudaGetLastError());
+    n->packed = false;
+    return SFSEG_OK;
+}
+
+}  // extern "C"

@@ -146,6 +146,7 @@ extern "C" int sfseg_power_iterate_noalloc(const sfseg_params* prm, int C, int T
             (e = cudaMemcpyAsync(&fl, flags, sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
             (e = cudaStreamSynchronize(s)) != cudaSuccess)
             return fail(SFSEG_ERR_CUDA, std::string("reading the norms: ") + cudaGetErrorString(e));
+        if (fl & kFlagTimeout) return fail(SFSEG_ERR_TIMEOUT, "a bounded wait for a TMA copy gave up");
         if (fl & kFlagBadFeature) return fail(SFSEG_ERR_NONFINITE, "features must be finite and >= 0");
         if (fl & kFlagNonfinite) return fail(SFSEG_ERR_NONFINITE, "an iterate norm became NaN or Inf");
         if (fl & kFlagZeroNorm) return fail(SFSEG_ERR_ZERO_NORM, "an iterate became zero");

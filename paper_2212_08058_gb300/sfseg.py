@@ -61,6 +61,15 @@ SIGNATURES = {
     "sfseg_enable_iter_timing": [_vp, _i],
     "sfseg_iter_timing": [_vp, _dp, ctypes.POINTER(ctypes.c_int64)],
     "sfseg_kernel_launches": [ctypes.POINTER(ctypes.c_int64)],
+    "sfseg_net_create": [_i, ctypes.c_uint64, ctypes.POINTER(_vp)],
+    "sfseg_net_destroy": [_vp],
+    "sfseg_net_num_params": [_vp, ctypes.POINTER(ctypes.c_int64)],
+    "sfseg_net_get_params": [_vp, _fp, ctypes.c_int64],
+    "sfseg_net_set_params": [_vp, _fp, ctypes.c_int64],
+    "sfseg_net_forward": [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp],
+    "sfseg_net_backward": [_vp, _vp, _i, _i, _i, _i, _i, _vp, _dp, _fp, _vp],
+    "sfseg_net_adamw": [_vp, _f, _f, _f, _f, _f, _vp],
+    "sfseg_warmstart": [_vp, _vp, _vp, _i, _vp, _vp],
     "sfseg_power_iterate_noalloc": [ctypes.POINTER(Params), _i, _i, _i, _i, _vp, _i, _fp, _f,
                                     ctypes.POINTER(Neighborhood), _i, _vp, _i, _dp, _vp],
 }
@@ -234,6 +243,13 @@ class PowerIteration:
         return loss.value, g
 
 
+    def warmstart(self, net: "WarmStartNet", features: torch.Tensor) -> torch.Tensor:
+        """x0 = net(features) for this handle's volume (sfseg_warmstart)."""
+        self._check_features(features)
+        x0 = torch.empty((self.T, self.H, self.W), device="cuda", dtype=torch.float32)
+        _check(lib().sfseg_warmstart(self._h, net._n, _ptr(features), _dtype_code(features), _ptr(x0), _stream()))
+        return x0
+
     def enable_iter_timing(self, on: bool = True):
         _check(lib().sfseg_enable_iter_timing(self._h, int(bool(on))))
 
@@ -243,6 +259,71 @@ class PowerIteration:
         n = ctypes.c_int64()
         _check(lib().sfseg_iter_timing(self._h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+
+class WarmStartNet:
+    """The learned warm-start network (sfseg_net_*): x0 = net(channels) on the tensor cores."""
+
+    def __init__(self, c_in: int = 8, seed: int = 0):
+        n = ctypes.c_void_p()
+        _check(lib().sfseg_net_create(int(c_in), ctypes.c_uint64(seed), ctypes.byref(n)))
+        self._n = n
+        self.c_in = c_in
+        cnt = ctypes.c_int64()
+        _check(lib().sfseg_net_num_params(self._n, ctypes.byref(cnt)))
+        self.num_params = cnt.value
+
+    def close(self):
+        if getattr(self, "_n", None):
+            lib().sfseg_net_destroy(self._n)
+            self._n = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        a = np.empty(self.num_params, dtype=np.float32)
+        _check(lib().sfseg_net_get_params(self._n, a.ctypes.data_as(_fp), a.size))
+        return a
+
+    def set_params(self, a) -> None:
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        _check(lib().sfseg_net_set_params(self._n, a.ctypes.data_as(_fp), a.size))
+
+    def unflatten(self, flat: np.ndarray):
+        """[(W1, b1), ..., (W4, b4)] with W as [out, 3, 3, 3, in] views of a flat vector."""
+        dims = [(32, self.c_in), (32, 32), (32, 32), (1, 32)]
+        out, o = [], 0
+        for co, ci in dims:
+            w = flat[o:o + co * 27 * ci].reshape(co, 3, 3, 3, ci)
+            o += co * 27 * ci
+            b = flat[o:o + co]
+            o += co
+            out.append((w, b))
+        return out
+
+    def forward(self, features: torch.Tensor) -> torch.Tensor:
+        C, T, H, W = features.shape
+        x0 = torch.empty((T, H, W), device="cuda", dtype=torch.float32)
+        _check(lib().sfseg_net_forward(self._n, _ptr(features), _dtype_code(features), C, T, H, W, _ptr(x0),
+                                       _stream()))
+        return x0
+
+    def backward(self, features: torch.Tensor, target: torch.Tensor, want_grads: bool = False):
+        C, T, H, W = features.shape
+        loss = ctypes.c_double()
+        g = np.empty(self.num_params, dtype=np.float32) if want_grads else None
+        _check(lib().sfseg_net_backward(self._n, _ptr(features), _dtype_code(features), C, T, H, W,
+                                        _ptr(target.contiguous()), ctypes.byref(loss),
+                                        g.ctypes.data_as(_fp) if g is not None else None, _stream()))
+        return (loss.value, g) if want_grads else loss.value
+
+    def adamw(self, lr: float = 1e-3, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8,
+              weight_decay: float = 0.0):
+        _check(lib().sfseg_net_adamw(self._n, lr, beta1, beta2, eps, weight_decay, _stream()))
 
 
 def kernel_launches() -> int:

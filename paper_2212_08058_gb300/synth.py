@@ -189,3 +189,49 @@ def multichannel_torch(T: int, H: int, W: int, C: int, seed: int, device, dtype=
     gm = -torch.log(torch.rand(C, generator=g, device=device))   # Gamma(1) = Exp(1)
     w = (gm / gm.sum()).float()
     return V, w
+
+
+def fixed_weights(C: int = 8, seed: int = 5999) -> np.ndarray:
+    """One Dirichlet(1) draw of channel weights, shared by every warm-start training volume and the
+    large inference volume (a deployed SFSeg++ has one learned weight vector)."""
+    g = np.random.default_rng(seed).gamma(1.0, 1.0, size=C)
+    return (g / g.sum()).astype(np.float32)
+
+
+def training_volume_torch(index: int, T: int = 16, H: int = 128, W: int = 128, C: int = 8,
+                          base_seed: int = 5000, device="cuda", scale_h: int = 1080):
+    """Training input ``index`` for the warm-start network, drawn on ``device``: 1 to 3 Gaussian
+    blobs whose width, speed and noise follow the statistics of a ``scale_h``-row video seen
+    through a H x W window (sigma between scale_h/16 and scale_h/6 pixels, so that a crop often
+    shows a blob edge rather than a whole blob), rendered as C noisy channels like
+    ``multichannel`` (shift in [-4, 4]^2, N(0, sigma_c^2) noise with sigma_c in [0.05, 0.3],
+    10 % dropped frames).  Returns V [C, T, H, W] float32 on the device."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(base_seed + index)
+
+    def u(lo, hi):
+        return lo + (hi - lo) * float(torch.rand(1, generator=g, device=device).item())
+
+    hh = torch.arange(H, device=device, dtype=torch.float32)[:, None]
+    ww = torch.arange(W, device=device, dtype=torch.float32)[None, :]
+    k = 1 + int(torch.randint(0, 3, (1,), generator=g, device=device).item())
+    blobs = []
+    for _ in range(k):
+        sg = u(scale_h / 16.0, scale_h / 6.0)
+        blobs.append((u(0.4, 1.0), sg, u(-sg, H + sg), u(-sg, W + sg), u(-H / 32, H / 32), u(-W / 32, W / 32)))
+    m = torch.zeros((T, H, W), device=device)
+    for t in range(T):
+        for amp, sg, h0, w0, vh, vw in blobs:
+            b = amp * torch.exp(-((hh - h0 - vh * t) ** 2 + (ww - w0 - vw * t) ** 2) / (2 * sg * sg))
+            m[t] = torch.maximum(m[t], b)
+    V = torch.empty((C, T, H, W), device=device)
+    sig = torch.linspace(0.05, 0.3, C).tolist()
+    n_drop = int(round(0.1 * T))
+    for c in range(C):
+        dy, dx = (int(v) for v in torch.randint(-4, 5, (2,), generator=g, device=device).tolist())
+        sh = torch.roll(m, shifts=(dy, dx), dims=(1, 2))
+        V[c] = (sh + torch.randn((T, H, W), generator=g, device=device) * sig[c]).clamp_(0.0, 1.0)
+        if n_drop:
+            V[c, torch.randperm(T, generator=g, device=device)[:n_drop]] = 0.0
+    return V

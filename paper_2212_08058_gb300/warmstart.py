@@ -1,0 +1,128 @@
+"""Warm start for the power iteration: training the network on eigenvectors the plain method
+produces, and the time-to-residual comparison of start vectors.
+
+Everything runs through the C ABI (libsfseg.so): labels come from sfseg_power_iterate with
+residual checks (sfseg_rayleigh), the network trains with sfseg_net_backward/sfseg_net_adamw, and
+the comparison times whole runs with CUDA events.
+"""
+from __future__ import annotations
+
+import os
+import time
+
+import numpy as np
+import torch
+
+from . import sfseg, synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_WEIGHTS = os.path.join(HERE, "data", "warmstart_c8.npy")
+
+
+def iterate_to_residual(h: sfseg.PowerIteration, radius, x: torch.Tensor, tol: float, chunk: int = 20,
+                        max_iters: int = 4000, bf16_until: float | None = None, init: str = "user"):
+    """Power-iterate from x until the Eq. 3 residual of the FP32 operator is <= tol, checking every
+    ``chunk`` iterations.  With ``bf16_until`` set, iterations keep bf16 storage while the residual
+    is above that value.  Returns (x, iterations, residual, residual trace)."""
+    its, trace = 0, []
+    rho, res = h.rayleigh(x, radius) if init == "user" else (None, float("inf"))
+    if init == "user":
+        trace.append((0, res))
+    first = init
+    while res > tol and its < max_iters:
+        nb = chunk if (bf16_until is not None and res > bf16_until) else 0
+        x = h.power_iterate(None, radius=radius, iters=chunk, iters_bf16=nb, x=x, init=first)
+        first = "user"
+        its += chunk
+        rho, res = h.rayleigh(x, radius)
+        trace.append((its, res))
+    return x, its, res, trace
+
+
+def make_label(h: sfseg.PowerIteration, feats: torch.Tensor, w, radius, tol: float = 1e-6,
+               max_iters: int = 3000) -> torch.Tensor:
+    """Eigenvector of the volume's operator from the plain method (uniform start)."""
+    h.set_features(feats, w, 0.0)
+    x = torch.empty((h.T, h.H, h.W), device="cuda")
+    x, _, _, _ = iterate_to_residual(h, radius, x, tol, chunk=50, max_iters=max_iters, init="uniform")
+    return x
+
+
+def train(net: sfseg.WarmStartNet, n_train: int = 2000, n_holdout: int = 100, epochs: int = 3,
+          lr: float = 1e-3, radius=(2, 7, 7), shape=(16, 128, 128), C: int = 8, log=print):
+    """Train ``net`` on ``n_train`` generated volumes labelled by the plain method; returns a dict
+    with the loss trace and the mean hold-out cosine loss before and after training."""
+    T, H, W = shape
+    w = synth.fixed_weights(C)
+    t0 = time.time()
+    vols, labels = [], []
+    with sfseg.PowerIteration(C, T, H, W) as h:
+        for i in range(n_train + n_holdout):
+            V = synth.training_volume_torch(i, T, H, W, C)
+            vols.append(V.to(torch.bfloat16))
+            labels.append(make_label(h, V, w, radius))
+    torch.cuda.synchronize()
+    t_label = time.time() - t0
+
+    def holdout():
+        return float(np.mean([net.backward(vols[i], labels[i]) for i in range(n_train, n_train + n_holdout)]))
+
+    before = holdout()
+    trace = []
+    t0 = time.time()
+    step = 0
+    for ep in range(epochs):
+        order = np.random.default_rng(ep).permutation(n_train)
+        run = 0.0
+        for i in order:
+            run += net.backward(vols[i], labels[i])
+            net.adamw(lr=lr * (0.3 if ep == epochs - 1 else 1.0), weight_decay=1e-4)
+            step += 1
+        trace.append(run / n_train)
+        log(f"epoch {ep}: mean training loss {trace[-1]:.4f}")
+    torch.cuda.synchronize()
+    t_train = time.time() - t0
+    after = holdout()
+    return {"holdout_before": before, "holdout_after": after, "trace": trace, "label_s": t_label,
+            "train_s": t_train, "steps": step}
+
+
+def save(net: sfseg.WarmStartNet, path: str = DEFAULT_WEIGHTS):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    np.save(path, net.get_params())
+
+
+def load(net: sfseg.WarmStartNet, path: str = DEFAULT_WEIGHTS) -> bool:
+    if not os.path.exists(path):
+        return False
+    net.set_params(np.load(path))
+    return True
+
+
+def compare_starts(feats: torch.Tensor, w, radius=(2, 7, 7), tol: float = 1e-4, net=None, chunk: int = 20,
+                   max_iters: int = 4000, bf16_until: float = 2e-3):
+    """Wall time (CUDA events, whole run including the network and every residual check) to reach
+    residual <= tol from (a) the uniform start with float32 storage, (b) the S_m start, (c) the
+    network's start with bf16 storage until residual bf16_until, then float32."""
+    C, T, H, W = feats.shape
+    out = {}
+    with sfseg.PowerIteration(C, T, H, W) as h:
+        h.set_features(feats, w, 0.0)
+        x = torch.empty((T, H, W), device="cuda")
+        h.power_iterate(None, radius=radius, iters=2, x=x)        # warm-up of every kernel
+        h.rayleigh(x, radius)
+        runs = [("uniform_f32", None, "uniform", None), ("smap_f32", None, "smap", None)]
+        if net is not None:
+            runs.append(("warmstart_bf16", net, "user", bf16_until))
+        for name, n, init, b16 in runs:
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            if n is not None:
+                x = h.warmstart(n, feats)
+            x, its, res, trace = iterate_to_residual(h, radius, x, tol, chunk, max_iters, b16, init)
+            e1.record()
+            torch.cuda.synchronize()
+            out[name] = {"ms": e0.elapsed_time(e1), "iterations": its, "residual": res,
+                         "trace": [(int(a), float(b)) for a, b in trace[:: max(1, len(trace) // 20)]]}
+    return out

@@ -78,6 +78,32 @@ def test_ragged_and_degenerate_shapes(shape, radius, sigma, alpha, p, K):
     np.testing.assert_allclose(nug, nuo, rtol=1e-5)
 
 
+@pytest.mark.parametrize("shape,radius", [
+    ((1, 5, 7), (2, 7, 7)),          # one frame, tile larger than the volume
+    ((3, 17, 65), (2, 7, 7)),        # one row and one column past a tile
+    ((4, 40, 72), (2, 7, 7)),
+    ((2, 9, 130), (1, 3, 3)),
+    ((6, 31, 200), (1, 3, 3)),
+    ((2, 16, 64), (1, 3, 3)),        # exactly one tile
+])
+def test_fast_kernel_shapes(shape, radius):
+    """The TMA kernel used for the method's radii: parity with the oracle, and with the generic
+    streaming kernel (which the library uses when checkpoints are recorded every step)."""
+    sf = _sf()
+    rng = np.random.default_rng(sum(shape) + 7)
+    V = rng.uniform(0.0, 1.0, size=(1, *shape)).astype(np.float32)
+    K = 9
+    xg, nug = _run(V, radius, K)
+    xo, nuo = _oracle(V, radius, K)
+    assert np.abs(xg - xo).max() <= TOL_F32
+    np.testing.assert_allclose(nug, nuo, rtol=1e-5)
+    with sf.PowerIteration(1, *shape) as h:
+        xr = h.power_iterate(torch.from_numpy(V).cuda(), radius=radius, iters=K, record_every=1)
+        torch.cuda.synchronize()
+        xr = xr.cpu().numpy().astype(np.float64)
+    assert np.abs(xg - xr).max() <= 1e-6
+
+
 def test_radius_zero_is_diagonal():
     """Radius (0, 0, 0): K steps from uniform give u^(2K)/||u^(2K)|| exactly."""
     rng = np.random.default_rng(5)
