@@ -32,12 +32,18 @@
 namespace sfseg {
 namespace fast {
 
-constexpr int TH = 16;         // tile rows
+#ifndef SFSEG_FAST_TH
+#define SFSEG_FAST_TH 16
+#endif
+#ifndef SFSEG_FAST_RHS
+#define SFSEG_FAST_RHS 8
+#endif
+constexpr int TH = SFSEG_FAST_TH;   // tile rows (at most 16: four rows per warp)
 constexpr int TW = 64;         // tile columns
 constexpr int PADW = 8;        // columns loaded left and right of the tile (16-byte aligned x)
 constexpr int BW = TW + 2 * PADW;   // TMA box width
 constexpr int QP = BW + 2;     // row pitch of the h-pass result (2 mod 32 avoids bank conflicts)
-constexpr int RHS = 8;         // output rows per h-pass item
+constexpr int RHS = SFSEG_FAST_RHS;   // output rows per h-pass item (divides TH)
 constexpr int NTHR = 128;
 constexpr long long kSpinLimit = 1ll << 26;   // bounded mbarrier wait
 // Resident CTAs per SM the register allocation targets, and TMA stages (2: frame t+1 in flight
@@ -114,6 +120,7 @@ struct Cfg {
     static constexpr int NVAL = 8 + 2 * RW + ODD;         // w-pass window values (aligned start)
     static constexpr int NPAIR = (NVAL + 1) / 2;
     static_assert(NHITEMS <= NTHR, "h-pass items must fit the CTA");
+    static_assert(TH % RHS == 0 && TH <= 16, "tile rows: a multiple of the h-pass item, at most 16");
     static_assert(RW <= PADW, "halo wider than the loaded pad");
 };
 
@@ -208,7 +215,7 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
         float2 fo[4];
 #pragma unroll
         for (int m = 0; m < 4; ++m) fo[m] = make_float2(0.f, 0.f);
-        if (to >= t0 && h < g.H) {
+        if (to >= t0 && h < g.H && wr < TH) {
             const TS* fg = reinterpret_cast<const TS*>(P.f) + ((int64_t)to * g.H + h) * g.pitch + wbase;
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
@@ -258,7 +265,7 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
         }
         // ---------------- w-pass: Q -> x[n], then the t-filter update
         float2 y[3][4];
-        {
+        if (wr < TH) {
             const int a0 = PADW + wcs * 8 - RW - C::ODD;   // even
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
@@ -290,7 +297,7 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
             }
         }
         // ---------------- Eq. 7 combination for frame to = tt - RT
-        if (to >= t0) {
+        if (to >= t0 && wr < TH) {
             float2 outv[4];
 #pragma unroll
             for (int m = 0; m < 4; ++m) {

@@ -126,3 +126,38 @@ def compare_starts(feats: torch.Tensor, w, radius=(2, 7, 7), tol: float = 1e-4, 
             out[name] = {"ms": e0.elapsed_time(e1), "iterations": its, "residual": res,
                          "trace": [(int(a), float(b)) for a, b in trace[:: max(1, len(trace) // 20)]]}
     return out
+
+
+def time_inference(T: int, H: int, W: int, C: int = 8, reps: int = 5, weights: str | None = DEFAULT_WEIGHTS):
+    """CUDA-event time of the warm-start network on a C x T x H x W bf16 volume (multichannel
+    recipe drawn on the device); returns a dict with ms per forward and TFLOP/s (2 x 27 x
+    (16*32 + 32*32 + 32*32 + 32*16) flops per voxel as computed, i.e. with the padded channels)."""
+    V, _ = synth.multichannel_torch(T, H, W, C, seed=5600, device="cuda", dtype=torch.bfloat16)
+    net = sfseg.WarmStartNet(C)
+    if weights:
+        load(net, weights)
+    x0 = net.forward(V)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        x0 = net.forward(V)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    flops = 2.0 * 27 * (16 * 32 + 32 * 32 + 32 * 32 + 32 * 16) * T * H * W
+    net.close()
+    return {"shape": [C, T, H, W], "ms": ms, "tflops_padded": flops / (ms * 1e-3) / 1e12,
+            "x0_positive": bool((x0 > 0).all().item())}
+
+
+if __name__ == "__main__":
+    import argparse
+    import json
+    ap = argparse.ArgumentParser(description="time the warm-start network's forward pass")
+    ap.add_argument("--shape", type=int, nargs=3, default=[32, 256, 512], metavar=("T", "H", "W"))
+    ap.add_argument("--reps", type=int, default=5)
+    args = ap.parse_args()
+    from . import build as _build
+    _build.build()
+    print(json.dumps(time_inference(*args.shape, reps=args.reps)))
