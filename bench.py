@@ -225,14 +225,15 @@ def bench_bf16_multichannel(sfseg, synth, steps: int = 10):
 
 
 def bench_time_to_residual(sfseg, synth, warmstart, tol: float = 1e-4):
-    """Wall time to the Eq. 3 residual tol on the C = 8 bf16 120 x 1080 x 1920 volume from three
-    starts: uniform with float32 storage, S_m with float32 storage, and the trained warm-start
-    network followed by bf16 storage until the residual reaches 2e-3, then float32."""
+    """Wall time to the Eq. 3 residual tol on the C = 8 bf16 120 x 1080 x 1920 volume from four
+    starts: uniform and S_m with float32 storage (the plain method), the coarse-to-fine start
+    (two coarser levels), and the trained network's refinement of it followed by bf16 storage
+    until the residual reaches 2e-3, then float32."""
     import torch
     T5, H5, W5 = 120, 1080, 1920
     V, _ = synth.multichannel_torch(T5, H5, W5, 8, seed=5500, device="cuda", dtype=torch.bfloat16)
     w = synth.fixed_weights(8)
-    net = sfseg.WarmStartNet(8)
+    net = sfseg.WarmStartNet(9)
     trained = warmstart.load(net)
     res = warmstart.compare_starts(V, w, RADIUS, tol=tol, net=net if trained else None, max_iters=3000)
     net.close()

@@ -139,6 +139,22 @@ int sfseg_rayleigh(sfseg_handle* h, const sfseg_neighborhood* nb, const float* x
 int sfseg_backward(sfseg_handle* h, const sfseg_neighborhood* nb, const float* grad_x,
                    float* grad_weights, float* grad_bias, void* stream);
 
+/* Coarse-to-fine start vector (the paper has no counterpart; it starts from a uniform vector
+ * or from S_m, Alg. 1 line 3).  The slowly converging components of the iterate are smooth at
+ * the scale of the objects, so the same Eq. 7 operator on a 2x-pooled volume (per level: f
+ * averaged over 2x2x2 blocks, Gaussian widths halved, radii scaled with them and at least 1)
+ * has nearly the same principal eigenvector at those scales at an eighth of the cost per
+ * iteration.  The coarsest of `levels` (1..4) levels is solved from the uniform start, each
+ * finer level from the trilinear upsampling of the coarser solution, each until the Eq. 3
+ * residual of its own operator is <= tol (checked every `check_every` iterations, at most
+ * `max_iters` per level); the finest coarse solution, upsampled to the handle's volume, is
+ * written to x0_out (device float32 [T][H][W]) for SFSEG_INIT_USER.  iters_out: host array of
+ * `levels` ints (iterations per level, index 0 = finest coarse level) or NULL.  Requires the
+ * features set; allocates the pyramid (about 1/7 of the handle's workspace) on first use.
+ * Synchronises. */
+int sfseg_coarse_start(sfseg_handle* h, const sfseg_neighborhood* nb, int levels, double tol,
+                       int max_iters, int check_every, float* x0_out, int* iters_out, void* stream);
+
 /* Learning loss: L = 1 - soft-IoU(xh, g), xh = x / max(x), soft-IoU = sum(xh g) /
  * sum(xh + g - xh g), and dL/dx (the max differentiated at its first argmax).
  * x, target: device [T][H][W] float32 of this handle's size; grad_x: device float32 or NULL;
@@ -168,27 +184,32 @@ int sfseg_net_num_params(sfseg_net* net, int64_t* count);
 int sfseg_net_get_params(sfseg_net* net, float* host, int64_t count);
 int sfseg_net_set_params(sfseg_net* net, const float* host, int64_t count);
 
-/* x0_out (device float32 [T][H][W]) = network(features), features device [C][T][H][W] in
- * `dtype` with C <= c_in.  Asynchronous. */
-int sfseg_net_forward(sfseg_net* net, const void* features, int dtype, int C, int T, int H, int W,
-                      float* x0_out, void* stream);
+/* x0_out (device float32 [T][H][W]) = network(features, extra), features device [C][T][H][W] in
+ * `dtype`; extra: NULL, or a device float32 [T][H][W] volume given to the network as channel C
+ * (e.g. the upsampled coarse solution of sfseg_coarse_start); C (+1 with extra) <= c_in.
+ * Asynchronous. */
+int sfseg_net_forward(sfseg_net* net, const void* features, int dtype, int C, const float* extra,
+                      int T, int H, int W, float* x0_out, void* stream);
 
 /* Training loss and gradients: L = 1 - <x0, target> / (||x0|| ||target||) for the network's x0
  * (the direction of the start vector is what power iteration uses).  target: device float32
- * [T][H][W].  Writes L to *loss (host) and, if grads_out is not NULL, the parameter gradients to
- * it (host, sfseg_net_num_params floats); keeps them for sfseg_net_adamw.  Synchronises. */
-int sfseg_net_backward(sfseg_net* net, const void* features, int dtype, int C, int T, int H, int W,
-                       const float* target, double* loss, float* grads_out, void* stream);
+ * [T][H][W]; features and extra as for sfseg_net_forward.  Writes L to *loss (host) and, if
+ * grads_out is not NULL, the parameter gradients to it (host, sfseg_net_num_params floats);
+ * keeps them for sfseg_net_adamw.  Synchronises. */
+int sfseg_net_backward(sfseg_net* net, const void* features, int dtype, int C, const float* extra,
+                       int T, int H, int W, const float* target, double* loss, float* grads_out,
+                       void* stream);
 
 /* One AdamW step (decoupled weight decay) with the gradients of the last sfseg_net_backward. */
 int sfseg_net_adamw(sfseg_net* net, float lr, float beta1, float beta2, float eps,
                     float weight_decay, void* stream);
 
 /* The start vector for this handle's volume: x0_out (device float32 [T][H][W], usable as
- * x_inout with SFSEG_INIT_USER) = network(features), features device [C][T][H][W] of the
- * handle's shape in `dtype`.  Asynchronous. */
-int sfseg_warmstart(sfseg_handle* h, sfseg_net* net, const void* features, int dtype, float* x0_out,
-                    void* stream);
+ * x_inout with SFSEG_INIT_USER) = network(features, x_coarse), features device [C][T][H][W] of
+ * the handle's shape in `dtype`, x_coarse NULL or the device float32 [T][H][W] output of
+ * sfseg_coarse_start (for a network built with one more input channel).  Asynchronous. */
+int sfseg_warmstart(sfseg_handle* h, sfseg_net* net, const void* features, int dtype,
+                    const float* x_coarse, float* x0_out, void* stream);
 
 /* Instrumentation (no counterpart in the paper).  When enabled, each sfseg_power_iterate call
  * records two CUDA events on its stream, before its first and after its last iteration-kernel

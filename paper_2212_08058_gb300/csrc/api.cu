@@ -1,5 +1,6 @@
 // api.cu -- the C ABI of libsfseg.so (declared in include/sfseg.h): argument checking, the
 // handle's device workspace, and the sequence of kernel launches of each call.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -82,6 +83,10 @@ struct sfseg_handle {
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
     int64_t timed_launches = 0;
+    // coarse pyramid for sfseg_coarse_start: child handles (C = 1, pooled f) and their x
+    std::vector<sfseg_handle*> lvl;
+    std::vector<float*> lvl_f, lvl_x;
+    std::vector<int> lvl_p;           // pool factors (t, h, w) from the previous level, 3 per level
 };
 
 static cudaEvent_t take_event(sfseg_handle* h) {
@@ -211,6 +216,9 @@ int sfseg_destroy(sfseg_handle* h) {
     cudaFree(h->gz);
     for (float* p : h->seg) cudaFree(p);
     cudaFree(h->dots);
+    for (sfseg_handle* c : h->lvl) sfseg_destroy(c);
+    for (float* p : h->lvl_f) cudaFree(p);
+    for (float* p : h->lvl_x) cudaFree(p);
     for (cudaEvent_t e : h->ev_free) cudaEventDestroy(e);
     for (auto& pr : h->ev_pending) {
         cudaEventDestroy(pr.first);
@@ -360,9 +368,10 @@ int sfseg_iter_timing(sfseg_handle* h, double* ms, int64_t* launches) {
     return SFSEG_OK;
 }
 
-int sfseg_warmstart(sfseg_handle* h, sfseg_net* net, const void* features, int dtype, float* x0_out, void* stream) {
+int sfseg_warmstart(sfseg_handle* h, sfseg_net* net, const void* features, int dtype, const float* x_coarse,
+                    float* x0_out, void* stream) {
     if (int rc = check_handle(h)) return rc;
-    return sfseg_net_forward(net, features, dtype, h->C, h->g.T, h->g.H, h->g.W, x0_out, stream);
+    return sfseg_net_forward(net, features, dtype, h->C, x_coarse, h->g.T, h->g.H, h->g.W, x0_out, stream);
 }
 
 int sfseg_kernel_launches(int64_t* count) {
@@ -467,6 +476,99 @@ int sfseg_backward(sfseg_handle* h, const sfseg_neighborhood* nb, const float* g
     if (int rc = read_flags(h, s)) return rc;
     for (int ch = 0; ch < h->C; ++ch) grad_weights[ch] = (float)wacc[ch];
     *grad_bias = (float)wacc[h->C];
+    return SFSEG_OK;
+}
+
+int sfseg_coarse_start(sfseg_handle* h, const sfseg_neighborhood* nb, int levels, double tol, int max_iters,
+                       int check_every, float* x0_out, int* iters_out, void* stream) {
+    if (int rc = check_handle(h)) return rc;
+    Taps tp;
+    if (int rc = make_taps(nb, &tp)) return rc;
+    if (!x0_out) return fail(SFSEG_ERR_INVALID_ARG, "null x0_out");
+    if (levels < 1 || levels > 4) return fail(SFSEG_ERR_INVALID_ARG, "levels must be in [1, 4]");
+    if (!(tol > 0.0) || max_iters < 1 || check_every < 1)
+        return fail(SFSEG_ERR_INVALID_ARG, "tol > 0, max_iters >= 1 and check_every >= 1 are required");
+    if (!h->features_set) return fail(SFSEG_ERR_STATE, "no features set");
+    cudaStream_t s = (cudaStream_t)stream;
+    // (re)build the pyramid when its depth or shape does not match
+    if ((int)h->lvl.size() != levels) {
+        for (sfseg_handle* c : h->lvl) sfseg_destroy(c);
+        for (float* p : h->lvl_f) cudaFree(p);
+        for (float* p : h->lvl_x) cudaFree(p);
+        h->lvl.clear();
+        h->lvl_f.clear();
+        h->lvl_x.clear();
+        h->lvl_p.clear();
+        int T = h->g.T, H = h->g.H, W = h->g.W;
+        sfseg_params prm{h->alpha, h->p};
+        for (int l = 0; l < levels; ++l) {
+            const int pt = T > 1 ? 2 : 1, ph = H > 1 ? 2 : 1, pw = W > 1 ? 2 : 1;
+            T = (T + pt - 1) / pt;
+            H = (H + ph - 1) / ph;
+            W = (W + pw - 1) / pw;
+            sfseg_handle* c = nullptr;
+            if (int rc = sfseg_create(&prm, 1, T, H, W, &c)) return rc;
+            h->lvl.push_back(c);
+            float *fb = nullptr, *xb = nullptr;
+            SFSEG_CUDA(cudaMalloc(&fb, sizeof(float) * (size_t)T * H * W));
+            SFSEG_CUDA(cudaMalloc(&xb, sizeof(float) * (size_t)T * H * W));
+            h->lvl_f.push_back(fb);
+            h->lvl_x.push_back(xb);
+            h->lvl_p.insert(h->lvl_p.end(), {pt, ph, pw});
+        }
+    }
+    // restriction of f, level by level
+    std::vector<sfseg_neighborhood> nbs((size_t)levels);
+    double scale[3] = {1.0, 1.0, 1.0};
+    for (int l = 0; l < levels; ++l) {
+        const sfseg_handle* fine = l == 0 ? h : h->lvl[l - 1];
+        sfseg_handle* c = h->lvl[l];
+        const int* pf = &h->lvl_p[3 * l];
+        launch_pool_f(fine->f32, fine->g, pf[0], pf[1], pf[2], c->g.T, c->g.H, c->g.W, h->lvl_f[l], s);
+        SFSEG_LAUNCHED();
+        if (int rc = sfseg_set_features(c, h->lvl_f[l], SFSEG_F32, nullptr, 0.f, s)) return rc;
+        // the same Gaussian in physical units: widths in coarse pixels, truncated at the same
+        // multiple of the width
+        const int r[3] = {nb->rt, nb->rh, nb->rw};
+        const float sg[3] = {nb->sigma_t, nb->sigma_h, nb->sigma_w};
+        int rl[3];
+        float sl[3];
+        for (int a = 0; a < 3; ++a) {
+            scale[a] *= pf[a];
+            sl[a] = (float)(sg[a] / scale[a]);
+            rl[a] = r[a] == 0 ? 0 : (int)std::max(1.0, std::floor(r[a] / scale[a] + 0.5));
+        }
+        nbs[(size_t)l] = sfseg_neighborhood{rl[0], rl[1], rl[2], sl[0], sl[1], sl[2]};
+    }
+    // coarsest level from the uniform start, then each finer level from the upsampled solution
+    for (int l = levels - 1; l >= 0; --l) {
+        sfseg_handle* c = h->lvl[l];
+        int init = SFSEG_INIT_UNIFORM;
+        if (l < levels - 1) {
+            const sfseg_handle* cc = h->lvl[l + 1];
+            const int* pf = &h->lvl_p[3 * (l + 1)];
+            launch_upsample(h->lvl_x[l + 1], cc->g.T, cc->g.H, cc->g.W, pf[0], pf[1], pf[2], c->g.T, c->g.H, c->g.W,
+                            h->lvl_x[l], s);
+            SFSEG_LAUNCHED();
+            init = SFSEG_INIT_USER;
+        }
+        int its = 0;
+        double res = 1e300;
+        while (its < max_iters && res > tol) {
+            const int k = std::min(check_every, max_iters - its);
+            if (int rc = sfseg_power_iterate(c, nullptr, 0, nullptr, 0.f, &nbs[(size_t)l], k, 0, h->lvl_x[l], init, 0,
+                                             nullptr, stream))
+                return rc;
+            init = SFSEG_INIT_USER;
+            its += k;
+            if (int rc = sfseg_rayleigh(c, &nbs[(size_t)l], h->lvl_x[l], nullptr, &res, stream)) return rc;
+        }
+        if (iters_out) iters_out[l] = its;
+    }
+    const int* pf = &h->lvl_p[0];
+    const sfseg_handle* c0 = h->lvl[0];
+    launch_upsample(h->lvl_x[0], c0->g.T, c0->g.H, c0->g.W, pf[0], pf[1], pf[2], h->g.T, h->g.H, h->g.W, x0_out, s);
+    SFSEG_LAUNCHED();
     return SFSEG_OK;
 }
 

@@ -1,15 +1,16 @@
 // kernels_fast.cu -- the power-iteration step of Eq. 7 for the radii the method is used with,
-// (rt, rh, rw) = (1, 3, 3) and (2, 7, 7), written for sm_103a.
+// (rt, rh, rw) = (1, 3, 3) and (2, 7, 7) (and the coarse-level radii (1, 4, 4), (1, 2, 2)),
+// written for sm_103a.
 //
-// One CTA (128 threads) owns a 16 x 64 tile of (h, w) and streams along t through a chunk of
-// frames.  Per incoming frame:
-//   1. TMA brings the raw halo tile of v (= u x~) and f into shared memory (16 + 2rh rows of
+// One CTA (128 threads, three per SM) owns a 15 x 64 tile of (h, w) and streams along t through
+// a chunk of frames.  Per incoming frame:
+//   1. TMA brings the raw halo tile of v (= u x~) and f into shared memory (15 + 2rh rows of
 //      80 columns; zero fill outside the volume gives the zero padding, also for whole frames
 //      before the first and after the last).  The copies of the next frames are in flight
 //      while frame t is computed.
-//   2. h-pass: a thread takes a column pair and 8 output rows; it walks down the 8 + 2rh input
-//      rows once, forms the three signals z1 = v, z2 = f^2 v, z3 = f v of each, and accumulates
-//      them into its 8 x 3 outputs with packed FP32 FMAs (FFMA2, one per column pair).
+//   2. h-pass: a thread takes a column pair and 5 output rows (40 pairs x 3 row groups = 120 of
+//      the 128 threads); it walks down the 5 + 2rh input rows once, forms the three signals z1 = v, z2 = f^2 v, z3 = f v of each, and accumulates
+//      them into its 5 x 3 outputs with packed FP32 FMAs (FFMA2, one per column pair).
 //   3. w-pass: a thread takes 8 output columns of one row; it loads its window of the h-pass
 //      result once (aligned float2 pairs; the odd-aligned pairs are rebuilt in registers) and
 //      feeds the three w-filtered signals straight into the t-filter, kept in registers in
@@ -33,10 +34,10 @@ namespace sfseg {
 namespace fast {
 
 #ifndef SFSEG_FAST_TH
-#define SFSEG_FAST_TH 16
+#define SFSEG_FAST_TH 15
 #endif
 #ifndef SFSEG_FAST_RHS
-#define SFSEG_FAST_RHS 8
+#define SFSEG_FAST_RHS 5
 #endif
 constexpr int TH = SFSEG_FAST_TH;   // tile rows (at most 16: four rows per warp)
 constexpr int TW = 64;         // tile columns
@@ -49,10 +50,10 @@ constexpr long long kSpinLimit = 1ll << 26;   // bounded mbarrier wait
 // Resident CTAs per SM the register allocation targets, and TMA stages (2: frame t+1 in flight
 // while t is computed; 3: t+1 and t+2).  Compile-time tuning knobs.
 #ifndef SFSEG_FAST_MINB
-#define SFSEG_FAST_MINB 2
+#define SFSEG_FAST_MINB 3
 #endif
 #ifndef SFSEG_FAST_NSTAGE
-#define SFSEG_FAST_NSTAGE 3
+#define SFSEG_FAST_NSTAGE 2
 #endif
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -458,19 +459,26 @@ static bool dispatch(const void* vin, int vin_type, void* out, int out_type, boo
 
 }  // namespace fast
 
+// Radii with a compiled kernel: the method's (1,3,3) and (2,7,7), and (1,4,4), (1,2,2), the
+// radii of (2,7,7) on 2x- and 4x-coarsened volumes (sfseg_coarse_start).
+#define SFSEG_FAST_RADII(X) X(1, 3, 3) X(2, 7, 7) X(1, 4, 4) X(1, 2, 2)
+
 bool fast_iterate_supported(const Taps& tp) {
-    return (tp.rt == 1 && tp.rh == 3 && tp.rw == 3) || (tp.rt == 2 && tp.rh == 7 && tp.rw == 7);
+#define SFSEG_IS(A, B, C) if (tp.rt == A && tp.rh == B && tp.rw == C) return true;
+    SFSEG_FAST_RADII(SFSEG_IS)
+#undef SFSEG_IS
+    return false;
 }
 
 bool launch_iterate_fast(const void* vin, int vin_type, void* out, int out_type, bool out_x, const void* f,
                          const Geom& g, const Taps& tp, float inv_alpha, float p, const double* acc_in,
                          double* acc_out, int* flags, cudaStream_t s) {
-    if (tp.rt == 1 && tp.rh == 3 && tp.rw == 3)
-        return fast::dispatch<1, 3, 3>(vin, vin_type, out, out_type, out_x, f, g, tp, inv_alpha, p, acc_in, acc_out,
-                                       flags, s);
-    if (tp.rt == 2 && tp.rh == 7 && tp.rw == 7)
-        return fast::dispatch<2, 7, 7>(vin, vin_type, out, out_type, out_x, f, g, tp, inv_alpha, p, acc_in, acc_out,
-                                       flags, s);
+#define SFSEG_GO(A, B, C)                                                                                   \
+    if (tp.rt == A && tp.rh == B && tp.rw == C)                                                             \
+        return fast::dispatch<A, B, C>(vin, vin_type, out, out_type, out_x, f, g, tp, inv_alpha, p, acc_in, \
+                                       acc_out, flags, s);
+    SFSEG_FAST_RADII(SFSEG_GO)
+#undef SFSEG_GO
     return false;
 }
 

@@ -1,0 +1,98 @@
+// kernels_multilevel.cu -- restriction and prolongation between a volume and its 2x-coarsened
+// copy, for starting the power iteration from a coarse solution.
+//
+// The slowly converging components of the iterate are smooth at the scale of the objects (the
+// spectral gap of the Eq. 7 operator shrinks with the size of the volume in pixels), so the
+// same operator on a pooled volume, with the Gaussian's widths measured in coarse pixels, has
+// nearly the same principal eigenvector at those scales and converges in as many iterations at
+// an eighth of the cost.  Upsampled, it is a start vector whose remaining error is local.
+#include "common.cuh"
+#include "launch.h"
+
+namespace sfseg {
+
+// out[Tc][Hc][Wc] = mean of f over the (pt x ph x pw) block that lies inside the volume.
+// f in the internal layout of `g`; out in caller layout (pitch Wc).
+__global__ void pool_f_kernel(const float* f, Geom g, int pt, int ph, int pw, int Tc, int Hc, int Wc, float* out) {
+    const int64_t N = (int64_t)Tc * Hc * Wc;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int tc = (int)(i / ((int64_t)Hc * Wc));
+        const int hc = (int)((i / Wc) % Hc);
+        const int wc = (int)(i % Wc);
+        float s = 0.f;
+        int n = 0;
+        for (int a = 0; a < pt; ++a) {
+            const int t = tc * pt + a;
+            if (t >= g.T) continue;
+            for (int b = 0; b < ph; ++b) {
+                const int h = hc * ph + b;
+                if (h >= g.H) continue;
+                for (int c = 0; c < pw; ++c) {
+                    const int w = wc * pw + c;
+                    if (w >= g.W) continue;
+                    s += f[((int64_t)t * g.H + h) * g.pitch + w];
+                    ++n;
+                }
+            }
+        }
+        out[i] = n ? s / (float)n : 0.f;
+    }
+}
+
+// Linear interpolation weights of destination index d on an axis coarsened by p (half-pixel
+// centres: source coordinate (d + 0.5) / p - 0.5, clamped to the coarse extent).
+__device__ __forceinline__ void lin(int d, int p, int nc, int& i0, int& i1, float& w1) {
+    if (p == 1) {
+        i0 = i1 = min(d, nc - 1);
+        w1 = 0.f;
+        return;
+    }
+    float src = (d + 0.5f) / (float)p - 0.5f;
+    src = fminf(fmaxf(src, 0.f), (float)(nc - 1));
+    i0 = (int)src;
+    i1 = min(i0 + 1, nc - 1);
+    w1 = src - (float)i0;
+}
+
+// x[T][H][W] (caller layout) = trilinear interpolation of xc[Tc][Hc][Wc].
+__global__ void upsample_kernel(const float* xc, int Tc, int Hc, int Wc, int pt, int ph, int pw, int T, int H, int W,
+                                float* x) {
+    const int64_t N = (int64_t)T * H * W;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int t = (int)(i / ((int64_t)H * W));
+        const int h = (int)((i / W) % H);
+        const int w = (int)(i % W);
+        int t0, t1, h0, h1, w0, w1i;
+        float at, ah, aw;
+        lin(t, pt, Tc, t0, t1, at);
+        lin(h, ph, Hc, h0, h1, ah);
+        lin(w, pw, Wc, w0, w1i, aw);
+        auto X = [&](int a, int b, int c) { return xc[((int64_t)a * Hc + b) * Wc + c]; };
+        const float c00 = X(t0, h0, w0) + aw * (X(t0, h0, w1i) - X(t0, h0, w0));
+        const float c01 = X(t0, h1, w0) + aw * (X(t0, h1, w1i) - X(t0, h1, w0));
+        const float c10 = X(t1, h0, w0) + aw * (X(t1, h0, w1i) - X(t1, h0, w0));
+        const float c11 = X(t1, h1, w0) + aw * (X(t1, h1, w1i) - X(t1, h1, w0));
+        const float c0 = c00 + ah * (c01 - c00);
+        const float c1 = c10 + ah * (c11 - c10);
+        x[i] = c0 + at * (c1 - c0);
+    }
+}
+
+static int grid_for(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    const int cap = 16 * num_sms();
+    return (int)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+void launch_pool_f(const float* f, Geom g, int pt, int ph, int pw, int Tc, int Hc, int Wc, float* out, cudaStream_t s) {
+    pool_f_kernel<<<grid_for((int64_t)Tc * Hc * Wc), 256, 0, s>>>(f, g, pt, ph, pw, Tc, Hc, Wc, out);
+    count_launches(1);
+}
+
+void launch_upsample(const float* xc, int Tc, int Hc, int Wc, int pt, int ph, int pw, int T, int H, int W, float* x,
+                     cudaStream_t s) {
+    upsample_kernel<<<grid_for((int64_t)T * H * W), 256, 0, s>>>(xc, Tc, Hc, Wc, pt, ph, pw, T, H, W, x);
+    count_launches(1);
+}
+
+}  // namespace sfseg

@@ -52,6 +52,12 @@ void launch_to_bf16(const float* a, __nv_bfloat16* b, int64_t n, cudaStream_t s)
 void launch_apply_user(const float* x, float* y, float* scratch_v, const float* f32, Geom g, const Taps& tp,
                        float inv_alpha, float p, int* flags, cudaStream_t s);
 
+// Restriction of f (internal layout) by (pt, ph, pw) into a caller-layout coarse volume, and
+// trilinear prolongation of a caller-layout coarse x (kernels_multilevel.cu).
+void launch_pool_f(const float* f, Geom g, int pt, int ph, int pw, int Tc, int Hc, int Wc, float* out, cudaStream_t s);
+void launch_upsample(const float* xc, int Tc, int Hc, int Wc, int pt, int ph, int pw, int T, int H, int W, float* x,
+                     cudaStream_t s);
+
 // x *= 1/sqrt(*acc) over a caller-layout volume.
 void launch_scale_inv_norm(float* x, int64_t n, const double* acc, int* flags, cudaStream_t s);
 

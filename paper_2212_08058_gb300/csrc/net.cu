@@ -305,13 +305,19 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
 }
 
 // ------------------------------------------------------------------------ small kernels
-// Caller's channels [C][T][H][W] (float or bf16) -> bf16 [T][H][W][16], channels >= C zero.
+// Caller's channels [C][T][H][W] (float or bf16), plus an optional float [T][H][W] channel after
+// them -> bf16 [T][H][W][16], remaining channels zero.
 template <typename TIn>
-__global__ void to_channels_last(const TIn* f, int C, int64_t N, __nv_bfloat16* out) {
+__global__ void to_channels_last(const TIn* f, int C, const float* extra, int64_t N, __nv_bfloat16* out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         __nv_bfloat16 v[16];
 #pragma unroll
-        for (int c = 0; c < 16; ++c) v[c] = __float2bfloat16_rn(c < C ? ldf(f + (int64_t)c * N + i) : 0.f);
+        for (int c = 0; c < 16; ++c) {
+            float a = 0.f;
+            if (c < C) a = ldf(f + (int64_t)c * N + i);
+            else if (c == C && extra) a = extra[i];
+            v[c] = __float2bfloat16_rn(a);
+        }
         uint4* o = reinterpret_cast<uint4*>(out + i * 16);
         o[0] = reinterpret_cast<const uint4*>(v)[0];
         o[1] = reinterpret_cast<const uint4*>(v)[1];
@@ -596,15 +602,17 @@ int check_flags(sfseg_net* n, cudaStream_t s) {
     return SFSEG_OK;
 }
 
-int net_forward(sfseg_net* n, const void* feats, int dtype, int C, int T, int H, int W, bool train, cudaStream_t s) {
+int net_forward(sfseg_net* n, const void* feats, int dtype, int C, const float* extra, int T, int H, int W, bool train,
+                cudaStream_t s) {
     const int64_t N = (int64_t)T * H * W;
     if (int rc = ensure_ws(n, N, train)) return rc;
     __nv_bfloat16* a3 = train ? n->a3 : n->a1;   // inference: layer 3 overwrites layer 1's output
     if (int rc = pack_all(n, s)) return rc;
     if (dtype == SFSEG_F32)
-        to_channels_last<float><<<blocks_for(N), 256, 0, s>>>((const float*)feats, C, N, n->x16);
+        to_channels_last<float><<<blocks_for(N), 256, 0, s>>>((const float*)feats, C, extra, N, n->x16);
     else
-        to_channels_last<__nv_bfloat16><<<blocks_for(N), 256, 0, s>>>((const __nv_bfloat16*)feats, C, N, n->x16);
+        to_channels_last<__nv_bfloat16><<<blocks_for(N), 256, 0, s>>>((const __nv_bfloat16*)feats, C, extra, N,
+                                                                       n->x16);
     count_launches(1);
     if (int rc = run_conv<16, 32, EPI_RELU>(n->x16, T, H, W, n->wf[0], n->p + n->off[1], n->a1, nullptr, nullptr,
                                             n->flags, s))
@@ -736,27 +744,29 @@ int sfseg_net_set_params(sfseg_net* n, const float* host, int64_t count) {
     return SFSEG_OK;
 }
 
-int sfseg_net_forward(sfseg_net* n, const void* features, int dtype, int C, int T, int H, int W, float* x0_out,
+int sfseg_net_forward(sfseg_net* n, const void* features, int dtype, int C, const float* extra, int T, int H, int W,
+                      float* x0_out,
                       void* stream) {
     if (!n || !x0_out) return nfail(SFSEG_ERR_INVALID_ARG, "null argument");
     if (int rc = check_vol(C, T, H, W, features)) return rc;
     if (dtype != SFSEG_F32 && dtype != SFSEG_BF16) return nfail(SFSEG_ERR_DTYPE, "dtype must be F32 or BF16");
-    if (C > n->cin) return nfail(SFSEG_ERR_SHAPE, "more channels than the network was built for");
+    if (C + (extra ? 1 : 0) > n->cin) return nfail(SFSEG_ERR_SHAPE, "more channels than the network was built for");
     cudaStream_t s = (cudaStream_t)stream;
-    if (int rc = net_forward(n, features, dtype, C, T, H, W, false, s)) return rc;
+    if (int rc = net_forward(n, features, dtype, C, extra, T, H, W, false, s)) return rc;
     NET_CUDA(cudaMemcpyAsync(x0_out, n->x0, (size_t)T * H * W * 4, cudaMemcpyDeviceToDevice, s));
     return SFSEG_OK;
 }
 
-int sfseg_net_backward(sfseg_net* n, const void* features, int dtype, int C, int T, int H, int W, const float* target,
+int sfseg_net_backward(sfseg_net* n, const void* features, int dtype, int C, const float* extra, int T, int H, int W,
+                       const float* target,
                        double* loss, float* grads_out, void* stream) {
     if (!n || !target || !loss) return nfail(SFSEG_ERR_INVALID_ARG, "null argument");
     if (int rc = check_vol(C, T, H, W, features)) return rc;
     if (dtype != SFSEG_F32 && dtype != SFSEG_BF16) return nfail(SFSEG_ERR_DTYPE, "dtype must be F32 or BF16");
-    if (C > n->cin) return nfail(SFSEG_ERR_SHAPE, "more channels than the network was built for");
+    if (C + (extra ? 1 : 0) > n->cin) return nfail(SFSEG_ERR_SHAPE, "more channels than the network was built for");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t N = (int64_t)T * H * W;
-    if (int rc = net_forward(n, features, dtype, C, T, H, W, true, s)) return rc;
+    if (int rc = net_forward(n, features, dtype, C, extra, T, H, W, true, s)) return rc;
     NET_CUDA(cudaMemsetAsync(n->acc, 0, 8 * sizeof(double), s));
     NET_CUDA(cudaMemsetAsync(n->g, 0, n->np * 4, s));
     cos_sums<<<blocks_for(N), 256, 0, s>>>(n->x0, target, N, n->acc);

@@ -58,6 +58,8 @@ SIGNATURES = {
     "sfseg_rayleigh": [_vp, ctypes.POINTER(Neighborhood), _vp, _dp, _dp, _vp],
     "sfseg_backward": [_vp, ctypes.POINTER(Neighborhood), _vp, _fp, _fp, _vp],
     "sfseg_soft_iou_loss": [_vp, _vp, _vp, _dp, _vp, _vp],
+    "sfseg_coarse_start": [_vp, ctypes.POINTER(Neighborhood), _i, ctypes.c_double, _i, _i, _vp,
+                           ctypes.POINTER(_i), _vp],
     "sfseg_enable_iter_timing": [_vp, _i],
     "sfseg_iter_timing": [_vp, _dp, ctypes.POINTER(ctypes.c_int64)],
     "sfseg_kernel_launches": [ctypes.POINTER(ctypes.c_int64)],
@@ -66,10 +68,10 @@ SIGNATURES = {
     "sfseg_net_num_params": [_vp, ctypes.POINTER(ctypes.c_int64)],
     "sfseg_net_get_params": [_vp, _fp, ctypes.c_int64],
     "sfseg_net_set_params": [_vp, _fp, ctypes.c_int64],
-    "sfseg_net_forward": [_vp, _vp, _i, _i, _i, _i, _i, _vp, _vp],
-    "sfseg_net_backward": [_vp, _vp, _i, _i, _i, _i, _i, _vp, _dp, _fp, _vp],
+    "sfseg_net_forward": [_vp, _vp, _i, _i, _vp, _i, _i, _i, _vp, _vp],
+    "sfseg_net_backward": [_vp, _vp, _i, _i, _vp, _i, _i, _i, _vp, _dp, _fp, _vp],
     "sfseg_net_adamw": [_vp, _f, _f, _f, _f, _f, _vp],
-    "sfseg_warmstart": [_vp, _vp, _vp, _i, _vp, _vp],
+    "sfseg_warmstart": [_vp, _vp, _vp, _i, _vp, _vp, _vp],
     "sfseg_power_iterate_noalloc": [ctypes.POINTER(Params), _i, _i, _i, _i, _vp, _i, _fp, _f,
                                     ctypes.POINTER(Neighborhood), _i, _vp, _i, _dp, _vp],
 }
@@ -243,11 +245,24 @@ class PowerIteration:
         return loss.value, g
 
 
-    def warmstart(self, net: "WarmStartNet", features: torch.Tensor) -> torch.Tensor:
-        """x0 = net(features) for this handle's volume (sfseg_warmstart)."""
-        self._check_features(features)
+    def coarse_start(self, radius=(2, 7, 7), sigma=None, levels: int = 2, tol: float = 1e-4,
+                     max_iters: int = 3000, check_every: int = 20):
+        """Start vector from the coarse-to-fine solve (sfseg_coarse_start); returns (x0, iterations
+        per level, finest first).  Needs the features set; synchronises."""
         x0 = torch.empty((self.T, self.H, self.W), device="cuda", dtype=torch.float32)
-        _check(lib().sfseg_warmstart(self._h, net._n, _ptr(features), _dtype_code(features), _ptr(x0), _stream()))
+        its = (ctypes.c_int * levels)()
+        _check(lib().sfseg_coarse_start(self._h, ctypes.byref(neighborhood(radius, sigma)), int(levels), float(tol),
+                                        int(max_iters), int(check_every), _ptr(x0), its, _stream()))
+        return x0, list(its)
+
+    def warmstart(self, net: "WarmStartNet", features: torch.Tensor, x_coarse: torch.Tensor | None = None) -> torch.Tensor:
+        """x0 = net(features[, x_coarse]) for this handle's volume (sfseg_warmstart)."""
+        self._check_features(features)
+        if x_coarse is not None:
+            self._check_volume(x_coarse, "x_coarse")
+        x0 = torch.empty((self.T, self.H, self.W), device="cuda", dtype=torch.float32)
+        _check(lib().sfseg_warmstart(self._h, net._n, _ptr(features), _dtype_code(features), _ptr(x_coarse),
+                                     _ptr(x0), _stream()))
         return x0
 
     def enable_iter_timing(self, on: bool = True):
@@ -305,18 +320,19 @@ class WarmStartNet:
             out.append((w, b))
         return out
 
-    def forward(self, features: torch.Tensor) -> torch.Tensor:
+    def forward(self, features: torch.Tensor, extra: torch.Tensor | None = None) -> torch.Tensor:
         C, T, H, W = features.shape
         x0 = torch.empty((T, H, W), device="cuda", dtype=torch.float32)
-        _check(lib().sfseg_net_forward(self._n, _ptr(features), _dtype_code(features), C, T, H, W, _ptr(x0),
-                                       _stream()))
+        _check(lib().sfseg_net_forward(self._n, _ptr(features), _dtype_code(features), C, _ptr(extra), T, H, W,
+                                       _ptr(x0), _stream()))
         return x0
 
-    def backward(self, features: torch.Tensor, target: torch.Tensor, want_grads: bool = False):
+    def backward(self, features: torch.Tensor, target: torch.Tensor, want_grads: bool = False,
+                 extra: torch.Tensor | None = None):
         C, T, H, W = features.shape
         loss = ctypes.c_double()
         g = np.empty(self.num_params, dtype=np.float32) if want_grads else None
-        _check(lib().sfseg_net_backward(self._n, _ptr(features), _dtype_code(features), C, T, H, W,
+        _check(lib().sfseg_net_backward(self._n, _ptr(features), _dtype_code(features), C, _ptr(extra), T, H, W,
                                         _ptr(target.contiguous()), ctypes.byref(loss),
                                         g.ctypes.data_as(_fp) if g is not None else None, _stream()))
         return (loss.value, g) if want_grads else loss.value

@@ -1,5 +1,6 @@
-"""Train the warm-start network on volumes labelled by the plain power iteration and save its
-parameters (paper_2212_08058_gb300/data/warmstart_c8.npy).
+"""Train the warm-start network (8 raw channels + the upsampled coarse solution) on volumes
+labelled by the plain power iteration and save its parameters
+(paper_2212_08058_gb300/data/warmstart_c8_coarse.npy).
 
     python -m paper_2212_08058_gb300.train_warmstart [--volumes 2000] [--epochs 3]
 
@@ -23,7 +24,7 @@ def main():
     ap.add_argument("--out", default=warmstart.DEFAULT_WEIGHTS)
     args = ap.parse_args()
     build.build()
-    net = sfseg.WarmStartNet(8, seed=args.seed)
+    net = sfseg.WarmStartNet(9, seed=args.seed)
     stats = warmstart.train(net, n_train=args.volumes, n_holdout=args.holdout, epochs=args.epochs, lr=args.lr,
                             log=lambda m: None)
     warmstart.save(net, args.out)

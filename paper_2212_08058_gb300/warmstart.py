@@ -16,7 +16,9 @@ import torch
 from . import sfseg, synth
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-DEFAULT_WEIGHTS = os.path.join(HERE, "data", "warmstart_c8.npy")
+DEFAULT_WEIGHTS = os.path.join(HERE, "data", "warmstart_c8_coarse.npy")
+COARSE_LEVELS_TRAIN = 1      # 16x128x128 training volumes: one 2x coarser level
+COARSE_TOL = 1e-4
 
 
 def iterate_to_residual(h: sfseg.PowerIteration, radius, x: torch.Tensor, tol: float, chunk: int = 20,
@@ -50,22 +52,32 @@ def make_label(h: sfseg.PowerIteration, feats: torch.Tensor, w, radius, tol: flo
 
 def train(net: sfseg.WarmStartNet, n_train: int = 2000, n_holdout: int = 100, epochs: int = 3,
           lr: float = 1e-3, radius=(2, 7, 7), shape=(16, 128, 128), C: int = 8, log=print):
-    """Train ``net`` on ``n_train`` generated volumes labelled by the plain method; returns a dict
-    with the loss trace and the mean hold-out cosine loss before and after training."""
+    """Train ``net`` (built with C + 1 input channels) on ``n_train`` generated volumes: its input
+    is the C raw channels plus the upsampled coarse solution (sfseg_coarse_start), its target the
+    eigenvector the plain method reaches (residual 1e-6).  Returns a dict with the loss trace, the
+    mean hold-out cosine loss before and after training, and that of the coarse start alone."""
     T, H, W = shape
     w = synth.fixed_weights(C)
     t0 = time.time()
-    vols, labels = [], []
+    vols, coarse, labels = [], [], []
     with sfseg.PowerIteration(C, T, H, W) as h:
         for i in range(n_train + n_holdout):
             V = synth.training_volume_torch(i, T, H, W, C)
+            labels.append(make_label(h, V, w, radius))     # sets the features
+            xc, _ = h.coarse_start(radius, levels=COARSE_LEVELS_TRAIN, tol=COARSE_TOL)
+            coarse.append(xc)
             vols.append(V.to(torch.bfloat16))
-            labels.append(make_label(h, V, w, radius))
     torch.cuda.synchronize()
     t_label = time.time() - t0
+    hold = range(n_train, n_train + n_holdout)
+
+    def cosine(a, b):
+        return float(1.0 - (a * b).sum() / (a.norm() * b.norm()))
+
+    coarse_only = float(np.mean([cosine(coarse[i], labels[i]) for i in hold]))
 
     def holdout():
-        return float(np.mean([net.backward(vols[i], labels[i]) for i in range(n_train, n_train + n_holdout)]))
+        return float(np.mean([net.backward(vols[i], labels[i], extra=coarse[i]) for i in hold]))
 
     before = holdout()
     trace = []
@@ -75,16 +87,16 @@ def train(net: sfseg.WarmStartNet, n_train: int = 2000, n_holdout: int = 100, ep
         order = np.random.default_rng(ep).permutation(n_train)
         run = 0.0
         for i in order:
-            run += net.backward(vols[i], labels[i])
+            run += net.backward(vols[i], labels[i], extra=coarse[i])
             net.adamw(lr=lr * (0.3 if ep == epochs - 1 else 1.0), weight_decay=1e-4)
             step += 1
         trace.append(run / n_train)
-        log(f"epoch {ep}: mean training loss {trace[-1]:.4f}")
+        log(f"epoch {ep}: mean training loss {trace[-1]:.5f}")
     torch.cuda.synchronize()
     t_train = time.time() - t0
     after = holdout()
-    return {"holdout_before": before, "holdout_after": after, "trace": trace, "label_s": t_label,
-            "train_s": t_train, "steps": step}
+    return {"holdout_before": before, "holdout_after": after, "holdout_coarse_only": coarse_only, "trace": trace,
+            "label_s": t_label, "train_s": t_train, "steps": step}
 
 
 def save(net: sfseg.WarmStartNet, path: str = DEFAULT_WEIGHTS):
@@ -100,10 +112,14 @@ def load(net: sfseg.WarmStartNet, path: str = DEFAULT_WEIGHTS) -> bool:
 
 
 def compare_starts(feats: torch.Tensor, w, radius=(2, 7, 7), tol: float = 1e-4, net=None, chunk: int = 20,
-                   max_iters: int = 4000, bf16_until: float = 2e-3):
-    """Wall time (CUDA events, whole run including the network and every residual check) to reach
-    residual <= tol from (a) the uniform start with float32 storage, (b) the S_m start, (c) the
-    network's start with bf16 storage until residual bf16_until, then float32."""
+                   max_iters: int = 4000, bf16_until: float = 2e-3, levels: int = 2):
+    """Wall time (CUDA events around the whole run: coarse solves, the network and every residual
+    check included) to reach residual <= tol on the volume from
+      uniform_f32       the uniform start, float32 storage (the plain method),
+      smap_f32          the S_m start (Alg. 1 line 3), float32 storage,
+      coarse_f32        the coarse-to-fine start (sfseg_coarse_start), float32 storage,
+      warmstart_bf16    the network's refinement of the coarse start, bf16 storage until the
+                        residual reaches bf16_until, then float32 (when a network is given)."""
     C, T, H, W = feats.shape
     out = {}
     with sfseg.PowerIteration(C, T, H, W) as h:
@@ -111,20 +127,28 @@ def compare_starts(feats: torch.Tensor, w, radius=(2, 7, 7), tol: float = 1e-4, 
         x = torch.empty((T, H, W), device="cuda")
         h.power_iterate(None, radius=radius, iters=2, x=x)        # warm-up of every kernel
         h.rayleigh(x, radius)
-        runs = [("uniform_f32", None, "uniform", None), ("smap_f32", None, "smap", None)]
+        h.coarse_start(radius, levels=levels, tol=1.0, max_iters=2)
+        runs = [("uniform_f32", "uniform", None), ("smap_f32", "smap", None), ("coarse_f32", "coarse", None)]
         if net is not None:
-            runs.append(("warmstart_bf16", net, "user", bf16_until))
-        for name, n, init, b16 in runs:
+            runs.append(("warmstart_bf16", "net", bf16_until))
+        for name, kind, b16 in runs:
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record()
-            if n is not None:
-                x = h.warmstart(n, feats)
+            coarse_its = None
+            init = "user"
+            if kind in ("coarse", "net"):
+                x, coarse_its = h.coarse_start(radius, levels=levels, tol=COARSE_TOL)
+                if kind == "net":
+                    x = h.warmstart(net, feats, x)
+            else:
+                init = kind
             x, its, res, trace = iterate_to_residual(h, radius, x, tol, chunk, max_iters, b16, init)
             e1.record()
             torch.cuda.synchronize()
             out[name] = {"ms": e0.elapsed_time(e1), "iterations": its, "residual": res,
-                         "trace": [(int(a), float(b)) for a, b in trace[:: max(1, len(trace) // 20)]]}
+                         "coarse_iterations": coarse_its,
+                         "trace": [(int(a), float(b)) for a, b in trace[:: max(1, len(trace) // 12)]]}
     return out
 
 
@@ -133,15 +157,16 @@ def time_inference(T: int, H: int, W: int, C: int = 8, reps: int = 5, weights: s
     recipe drawn on the device); returns a dict with ms per forward and TFLOP/s (2 x 27 x
     (16*32 + 32*32 + 32*32 + 32*16) flops per voxel as computed, i.e. with the padded channels)."""
     V, _ = synth.multichannel_torch(T, H, W, C, seed=5600, device="cuda", dtype=torch.bfloat16)
-    net = sfseg.WarmStartNet(C)
+    net = sfseg.WarmStartNet(C + 1)
     if weights:
         load(net, weights)
-    x0 = net.forward(V)
+    extra = torch.rand((T, H, W), device="cuda")
+    x0 = net.forward(V, extra)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for _ in range(reps):
-        x0 = net.forward(V)
+        x0 = net.forward(V, extra)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / reps
