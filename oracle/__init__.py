@@ -15,6 +15,8 @@ What each function computes, and the passage it follows:
 ``power_csr``                 Eq. 4 power iteration + Eq. 8 renormalisation on that matrix
 ``filter_apply``              Eq. 7 three-Gaussian-filter form (returns M x / alpha)
 ``power_filter``              Eq. 7 + Eq. 8 iterated (for volumes too large for a matrix)
+``soft_binarize``             Alg. 1 step 3 / Sec. 4.1 soft-binarisation iterations and the
+                              final hard threshold
 ``rayleigh``                  Eq. 3 Rayleigh quotient and the eigen-residual ||Mx - rho x|| / rho
 ``grad_csr``                  derivative of a loss of x_K w.r.t. the Eq. 9 weights (Sec. 3.4)
 ``soft_iou_loss``             1 - soft-IoU of the max-normalised x against a target mask
@@ -26,7 +28,9 @@ Readings of the paper that these functions take (the paper is silent or garbled 
 the sigmoid is the standard logistic 1/(1+e^-z); the operator between the second and third
 lines of Eq. 6 is "+"; the Eq. 7 filter operator is A = M/alpha; the Gaussian is
 exp(-0.5 sum_a d_a^2 / sigma_a^2), unnormalised, truncated to the box of radii (rt, rh, rw);
-the border is zero padding; every frame is updated each iteration.
+the border is zero padding; every frame is updated each iteration; the soft-binarisation
+sigmoid acts on the new vector scaled to maximum 1, x <- sigmoid(gain (y / max y - center)),
+and the hard segmentation is x > 1/2.
 """
 from __future__ import annotations
 
@@ -197,6 +201,26 @@ def power_filter(s, f, p: float, alpha: float, radius, x0, K: int, sigma=None):
     if rc != 0:
         raise FloatingPointError("zero norm in power iteration")
     return x, nu[:K]
+
+
+def soft_binarize(s, f, p: float, alpha: float, radius, x0, K: int, gain: float, center: float = 0.5,
+                  sigma=None):
+    """Alg. 1 step 3 (Sec. 4.1): K soft-binarisation steps x <- sigmoid(gain (y / max y - center)),
+    y = A x (Eq. 7), from x0.  Returns (x_K, hard mask x_K > 1/2 as uint8)."""
+    s = _c64(s)
+    f = _c64(f)
+    T, H, W = s.shape
+    rt, rh, rw = radius
+    st, sh, sw = default_sigma(radius) if sigma is None else sigma
+    x0 = _c64(x0).reshape(T, H, W)
+    x = np.empty_like(x0)
+    rc = _load().orc_soft_binarize(T, H, W, _d(s), _d(f), ctypes.c_double(p), ctypes.c_double(alpha),
+                                   rt, rh, rw, ctypes.c_double(st), ctypes.c_double(sh),
+                                   ctypes.c_double(sw), _d(x0), int(K), ctypes.c_double(gain),
+                                   ctypes.c_double(center), _d(x))
+    if rc != 0:
+        raise FloatingPointError("max(A x) <= 0 in a soft-binarisation step")
+    return x, (x > 0.5).astype(np.uint8)
 
 
 def sumsq(x) -> float:

@@ -258,6 +258,30 @@ int orc_power_filter(int T, int H, int W, const double* s, const double* f, doub
     return 0;
 }
 
+/* Soft-binarisation iterations (Alg. 1 step 3, Sec. 4.1): after the continuous iterations,
+ * each further step applies the Eq. 7 operator and then a sigmoid that pushes the solution
+ * towards {0, 1}.  Reading taken here (the paper names only "a sigmoid controlled by a
+ * parameter"): the new vector is first scaled to maximum 1, then
+ *     x <- 1 / (1 + exp(-gain (y / max(y) - center))),   y = A x,
+ * so the gain and the centre act on a [0, 1] scale whatever the size of the volume.  K steps
+ * from x0 (any positive scale).  Returns 0, or -1 if max(y) <= 0 in some step. */
+int orc_soft_binarize(int T, int H, int W, const double* s, const double* f, double p, double alpha,
+                      int rt, int rh, int rw, double st, double sh, double sw,
+                      const double* x0, int K, double gain, double center, double* x_out) {
+    int64_t N = (int64_t)T * H * W;
+    double* y = (double*)malloc((size_t)N * sizeof(double));
+    for (int64_t i = 0; i < N; ++i) x_out[i] = x0[i];
+    for (int k = 0; k < K; ++k) {
+        orc_filter_apply(T, H, W, s, f, p, alpha, rt, rh, rw, st, sh, sw, x_out, y);
+        double m = y[0];
+        for (int64_t i = 1; i < N; ++i) m = y[i] > m ? y[i] : m;
+        if (!(m > 0.0)) { free(y); return -1; }
+        for (int64_t i = 0; i < N; ++i) x_out[i] = 1.0 / (1.0 + exp(-gain * (y[i] / m - center)));
+    }
+    free(y);
+    return 0;
+}
+
 /* Partial derivative of the Eq. 2 pair kernel k(a, b) = a^p b^p (1 - alpha (a - b)^2) with
  * respect to its first argument (a > 0 required when p < 1). */
 static double dk_da(double a, double b, double p, double alpha) {

@@ -351,3 +351,64 @@ def test_warmstart_network_gradient_matches_finite_differences():
         fd = (oracle.warmstart_backward(feats, pp, target)[0]
               - oracle.warmstart_backward(feats, pm, target)[0]) / (2 * h)
         assert abs(fd - grads[li][0][idx]) < 1e-7 * max(1.0, abs(fd))
+
+
+# ------------------------------------------------------------ Alg. 1 step 3, Sec. 4.1
+def test_soft_binarize_kronecker_closed_form():
+    """Constant f and x0 = the top eigenvector v of A (the Kronecker product of 1D dense
+    eigenvectors, as above): y = lambda v, so one step gives sigmoid(gain (v / max v - c)) for any
+    positive scale of x0.  Catches a dropped max scaling, a flipped sigmoid and a lost centre."""
+    T, H, W = 4, 9, 11
+    r = (1, 3, 2)
+    sig = (0.8, 1.6, 1.1)
+    f = np.full((T, H, W), 0.6)
+
+    def band(n, ra, sa):
+        d = np.arange(n)[:, None] - np.arange(n)[None, :]
+        return np.where(np.abs(d) <= ra, np.exp(-d * d / (2 * sa * sa)), 0.0)
+
+    vecs = []
+    for n, ra, sa in zip((T, H, W), r, sig):
+        _, V = np.linalg.eigh(band(n, ra, sa))
+        vecs.append(np.abs(V[:, -1]))
+    v = np.einsum("a,b,c->abc", *vecs)
+    gain, c = 7.0, 0.55
+    want = scipy.special.expit(gain * (v / v.max() - c))
+    for scale in (1.0, 3.7e-4):
+        x, mask = oracle.soft_binarize(f, f, 0.4, 0.9, r, scale * v, 1, gain, c, sigma=sig)
+        np.testing.assert_allclose(x, want, rtol=1e-12, atol=1e-14)
+        np.testing.assert_array_equal(mask, (want > 0.5).astype(np.uint8))
+
+
+def test_soft_binarize_diagonal_two_steps():
+    """Radius (0, 0, 0): A = diag(u^2 / alpha), so y = u^2 x / alpha and two steps from the
+    uniform start are a closed form in u (catches steps applied in the wrong order, e.g. the
+    sigmoid before the operator)."""
+    rng = np.random.default_rng(17)
+    f = _rand_volume(rng, 2, 5, 6, lo=0.1)
+    p, alpha, gain, c = 0.45, 0.7, 5.0, 0.4
+    u2 = f ** (2 * p)
+    y1 = u2 / alpha
+    x1 = scipy.special.expit(gain * (y1 / y1.max() - c))
+    y2 = u2 * x1 / alpha
+    x2 = scipy.special.expit(gain * (y2 / y2.max() - c))
+    x, _ = oracle.soft_binarize(f, f, p, alpha, (0, 0, 0), np.ones(f.shape), 2, gain, c)
+    np.testing.assert_allclose(x, x2, rtol=1e-13)
+
+
+def test_soft_binarize_gain_limits():
+    """gain 0: every voxel is sigmoid(0) = 1/2 exactly.  Large gain: x approaches the indicator
+    of y / max y > c, and the hard mask equals it wherever y / max y is not within 1/gain of c."""
+    rng = np.random.default_rng(3)
+    f = _rand_volume(rng, 3, 12, 10, lo=0.05)
+    x0 = rng.uniform(0.2, 1.0, size=f.shape)
+    x, mask = oracle.soft_binarize(f, f, 0.5, 1.0, (1, 2, 2), x0, 1, 0.0, 0.5)
+    assert np.all(x == 0.5) and not mask.any()
+    y = oracle.filter_apply(f, f, 0.5, 1.0, (1, 2, 2), x0)
+    q = y / y.max()
+    gain = 1e4
+    x, mask = oracle.soft_binarize(f, f, 0.5, 1.0, (1, 2, 2), x0, 1, gain, 0.5)
+    clear = np.abs(q - 0.5) > 10.0 / gain
+    assert clear.mean() > 0.9
+    np.testing.assert_array_equal(mask[clear], (q[clear] > 0.5).astype(np.uint8))
+    assert np.all(np.abs(x[clear] - (q[clear] > 0.5)) < 1e-4)

@@ -38,6 +38,14 @@ MUTANTS = [
      "orc_spmv(N, rowptr, col, val, x_out, y);\n        double nu = 0.0;\n"
      "        for (int64_t q = 0; q < N; ++q) nu += fabs(y[q]);",
      ["test_two_node_closed_form", "test_power_iteration_matches_dense_eigensolver"]),
+    ("binarize_no_max_scaling", "exp(-gain * (y[i] / m - center))", "exp(-gain * (y[i] - center))",
+     ["test_soft_binarize_kronecker_closed_form"]),
+    ("binarize_sigmoid_sign", "exp(-gain * (y[i] / m - center))", "exp(gain * (y[i] / m - center))",
+     ["test_soft_binarize_kronecker_closed_form"]),
+    ("binarize_operator_skipped",
+     "orc_filter_apply(T, H, W, s, f, p, alpha, rt, rh, rw, st, sh, sw, x_out, y);\n        double m = y[0];",
+     "for (int64_t q = 0; q < N; ++q) y[q] = x_out[q];\n        double m = y[0];",
+     ["test_soft_binarize_diagonal_two_steps"]),
 ]
 
 
