@@ -224,6 +224,36 @@ def bench_bf16_multichannel(sfseg, synth, steps: int = 10):
             "hbm_frac_of_measured": 6.0 * nvox / (it_ms * 1e-3 / max(it_n, 1)) / 1e9 / _peaks()[0]}
 
 
+def bench_soft_binarize(sfseg, synth, steps: int = 5, tail: int = 10):
+    """Alg. 1 end to end on the 64 x 480 x 854 crossing-blobs volume at radius (2,7,7): 50
+    continuous iterations, then `tail` soft-binarisation steps (Alg. 1 step 3).  Reports the
+    wall time of one soft-binarisation step (CUDA events) and its share of the run."""
+    import torch
+    V = torch.from_numpy(synth.crossing_blobs(T, H, W, seed=SEED)).cuda()
+    h = sfseg.PowerIteration(1, T, H, W)
+    h.set_features(V)
+    x = h.power_iterate(None, radius=RADIUS, iters=ITERS)
+    for _ in range(2):
+        h.soft_binarize(x, RADIUS, iters=tail, gain=10.0)
+    torch.cuda.synchronize()
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    t_cont = t_tail = 0.0
+    for _ in range(steps):
+        e[0].record()
+        xc = h.power_iterate(None, radius=RADIUS, iters=ITERS, x=x)
+        e[1].record()
+        xs, mask = h.soft_binarize(xc, RADIUS, iters=tail, gain=10.0)
+        e[2].record()
+        torch.cuda.synchronize()
+        t_cont += e[0].elapsed_time(e[1])
+        t_tail += e[1].elapsed_time(e[2])
+    fg = float(mask.float().mean())
+    h.close()
+    return {"workload": f"Alg. 1 on plain SFSeg 480p: {ITERS} continuous + {tail} soft-binarisation steps, gain 10",
+            "ms_per_continuous_iteration": t_cont / steps / ITERS, "ms_per_binarize_step": t_tail / steps / tail,
+            "foreground_fraction": fg}
+
+
 def bench_time_to_residual(sfseg, synth, warmstart, tol: float = 1e-4):
     """Wall time to the Eq. 3 residual tol on the C = 8 bf16 120 x 1080 x 1920 volume from four
     starts: uniform and S_m with float32 storage (the plain method), the coarse-to-fine start
@@ -372,6 +402,7 @@ def main():
         if world == 1 and not args.no_extras:
             from paper_2212_08058_gb300 import warmstart
             out["bf16_multichannel"] = bench_bf16_multichannel(sfseg, synth)
+            out["soft_binarize"] = bench_soft_binarize(sfseg, synth)
             out["time_to_residual"] = bench_time_to_residual(sfseg, synth, warmstart)
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
