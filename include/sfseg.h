@@ -147,13 +147,28 @@ int sfseg_backward(sfseg_handle* h, const sfseg_neighborhood* nb, const float* g
  * iteration.  The coarsest of `levels` (1..4) levels is solved from the uniform start, each
  * finer level from the trilinear upsampling of the coarser solution, each until the Eq. 3
  * residual of its own operator is <= tol (checked every `check_every` iterations, at most
- * `max_iters` per level); the finest coarse solution, upsampled to the handle's volume, is
- * written to x0_out (device float32 [T][H][W]) for SFSEG_INIT_USER.  iters_out: host array of
+ * `max_iters` per level); the finest coarse solution, upsampled to the handle's volume and
+ * scaled to maximum 1, is written to x0_out (device float32 [T][H][W]) for SFSEG_INIT_USER.  iters_out: host array of
  * `levels` ints (iterations per level, index 0 = finest coarse level) or NULL.  Requires the
  * features set; allocates the pyramid (about 1/7 of the handle's workspace) on first use.
  * Synchronises. */
 int sfseg_coarse_start(sfseg_handle* h, const sfseg_neighborhood* nb, int levels, double tol,
                        int max_iters, int check_every, float* x0_out, int* iters_out, void* stream);
+
+/* Soft-binarisation iterations (Alg. 1 step 3, Sec. 4.1), run after the continuous power
+ * iterations.  Each of the `iters` steps computes y = A x (Eq. 7 operator, FP32) and then
+ *     x <- 1 / (1 + exp(-gain (y / max(y) - center)))
+ * (reading: the paper's "sigmoid controlled by a parameter" acts on the new vector scaled to
+ * maximum 1, so gain and center are independent of the volume size; gain 0 gives 1/2
+ * everywhere, large gains approach the indicator of y > center * max y).
+ *   x_inout: device float32 [T][H][W]; on input the continuous solution (any positive scale,
+ *            e.g. the output of sfseg_power_iterate), on output the soft segmentation in (0, 1).
+ *   mask_out: device uint8 [T][H][W] or NULL; receives the hard segmentation x > 1/2 (0 or 1).
+ *   iters >= 1; gain >= 0 and center finite.
+ * Requires the features set.  Errors: ZERO_NORM if max(y) <= 0 in a step (x then stays as the
+ * previous step left it).  Synchronises (reads the status flags). */
+int sfseg_soft_binarize(sfseg_handle* h, const sfseg_neighborhood* nb, int iters, float gain,
+                        float center, float* x_inout, unsigned char* mask_out, void* stream);
 
 /* Learning loss: L = 1 - soft-IoU(xh, g), xh = x / max(x), soft-IoU = sum(xh g) /
  * sum(xh + g - xh g), and dL/dx (the max differentiated at its first argmax).

@@ -568,8 +568,42 @@ int sfseg_coarse_start(sfseg_handle* h, const sfseg_neighborhood* nb, int levels
     const int* pf = &h->lvl_p[0];
     const sfseg_handle* c0 = h->lvl[0];
     launch_upsample(h->lvl_x[0], c0->g.T, c0->g.H, c0->g.W, pf[0], pf[1], pf[2], h->g.T, h->g.H, h->g.W, x0_out, s);
+    // maximum 1, so that the start vector's scale does not depend on the volume size (it is an
+    // input channel of the warm-start network)
+    launch_scale_by_max(x0_out, h->N, reinterpret_cast<unsigned*>(h->scratch + 60), s);
     SFSEG_LAUNCHED();
     return SFSEG_OK;
+}
+
+int sfseg_soft_binarize(sfseg_handle* h, const sfseg_neighborhood* nb, int iters, float gain, float center,
+                        float* x_inout, unsigned char* mask_out, void* stream) {
+    if (int rc = check_handle(h)) return rc;
+    Taps tp;
+    if (int rc = make_taps(nb, &tp)) return rc;
+    if (!x_inout) return fail(SFSEG_ERR_INVALID_ARG, "null x_inout");
+    if (iters < 1 || iters > (1 << 20)) return fail(SFSEG_ERR_INVALID_ARG, "iters must be in [1, 2^20]");
+    if (!(gain >= 0.f) || !std::isfinite(gain) || !std::isfinite(center))
+        return fail(SFSEG_ERR_INVALID_ARG, "gain must be finite and >= 0, center finite");
+    if (!h->features_set) return fail(SFSEG_ERR_STATE, "no features set");
+    cudaStream_t s = (cudaStream_t)stream;
+    const float inv_alpha = (float)(1.0 / h->alpha), p = (float)h->p;
+    float* y = (float*)h->vbuf[0];                     // A x, caller layout
+    float* v = (float*)h->vbuf[1];                     // u * x, internal layout
+    unsigned* key = reinterpret_cast<unsigned*>(h->scratch + 60);
+    const bool fast = fast_iterate_supported(tp);
+    for (int k = 0; k < iters; ++k) {
+        const bool last = k == iters - 1;
+        if (k == 0 || !fast)
+            launch_apply_user(x_inout, y, v, h->f32, h->g, tp, inv_alpha, p, h->flags, s);
+        else if (!launch_iterate_fast(v, kF32, y, kF32, true, h->f32, h->g, tp, inv_alpha, p, nullptr, nullptr,
+                                      h->flags, s))
+            return fail(SFSEG_ERR_CUDA, "stencil launch failed");
+        launch_max_key(y, h->N, key, s);
+        launch_sigmoid_step(y, key, gain, center, h->f32, p, h->g, x_inout, (fast && !last) ? v : nullptr,
+                            last ? mask_out : nullptr, h->flags, s);
+        SFSEG_LAUNCHED();
+    }
+    return read_flags(h, s);
 }
 
 int sfseg_soft_iou_loss(sfseg_handle* h, const float* x, const float* target, double* loss, float* grad_x,

@@ -8,6 +8,7 @@
 // an eighth of the cost.  Upsampled, it is a start vector whose remaining error is local.
 #include "common.cuh"
 #include "launch.h"
+#include "order_key.cuh"
 
 namespace sfseg {
 
@@ -78,6 +79,16 @@ __global__ void upsample_kernel(const float* xc, int Tc, int Hc, int Wc, int pt,
     }
 }
 
+// x /= max(x), the maximum given as an order-preserving key (no-op unless it is positive and
+// finite).
+__global__ void scale_by_max_kernel(float* x, int64_t n, const unsigned* key) {
+    const float m = order_value(*key);
+    if (!(m > 0.f) || isinf(m)) return;
+    const float inv = 1.f / m;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] *= inv;
+}
+
 static int grid_for(int64_t n) {
     int64_t b = (n + 255) / 256;
     const int cap = 16 * num_sms();
@@ -92,6 +103,12 @@ void launch_pool_f(const float* f, Geom g, int pt, int ph, int pw, int Tc, int H
 void launch_upsample(const float* xc, int Tc, int Hc, int Wc, int pt, int ph, int pw, int T, int H, int W, float* x,
                      cudaStream_t s) {
     upsample_kernel<<<grid_for((int64_t)T * H * W), 256, 0, s>>>(xc, Tc, Hc, Wc, pt, ph, pw, T, H, W, x);
+    count_launches(1);
+}
+
+void launch_scale_by_max(float* x, int64_t n, unsigned* key, cudaStream_t s) {
+    launch_max_key(x, n, key, s);
+    scale_by_max_kernel<<<grid_for(n), 256, 0, s>>>(x, n, key);
     count_launches(1);
 }
 

@@ -57,6 +57,15 @@ void launch_apply_user(const float* x, float* y, float* scratch_v, const float* 
 void launch_pool_f(const float* f, Geom g, int pt, int ph, int pw, int Tc, int Hc, int Wc, float* out, cudaStream_t s);
 void launch_upsample(const float* xc, int Tc, int Hc, int Wc, int pt, int ph, int pw, int T, int H, int W, float* x,
                      cudaStream_t s);
+// x /= max(x) over n caller-layout values (key: one unsigned of scratch).
+void launch_scale_by_max(float* x, int64_t n, unsigned* key, cudaStream_t s);
+
+// Soft-binarisation step pieces (kernels_tail.cu): *key = order-preserving key of max(y) over
+// n caller-layout values (the key is reset first); x = sigmoid(gain (y / max y - center)) with
+// optional v = u * x (internal layout) and mask = (x > 1/2).
+void launch_max_key(const float* y, int64_t n, unsigned* key, cudaStream_t s);
+void launch_sigmoid_step(const float* y, const unsigned* key, float gain, float center, const float* f32, float p,
+                         Geom g, float* x, float* v, unsigned char* mask, int* flags, cudaStream_t s);
 
 // x *= 1/sqrt(*acc) over a caller-layout volume.
 void launch_scale_inv_norm(float* x, int64_t n, const double* acc, int* flags, cudaStream_t s);

@@ -58,6 +58,7 @@ SIGNATURES = {
     "sfseg_rayleigh": [_vp, ctypes.POINTER(Neighborhood), _vp, _dp, _dp, _vp],
     "sfseg_backward": [_vp, ctypes.POINTER(Neighborhood), _vp, _fp, _fp, _vp],
     "sfseg_soft_iou_loss": [_vp, _vp, _vp, _dp, _vp, _vp],
+    "sfseg_soft_binarize": [_vp, ctypes.POINTER(Neighborhood), _i, _f, _f, _vp, _vp, _vp],
     "sfseg_coarse_start": [_vp, ctypes.POINTER(Neighborhood), _i, ctypes.c_double, _i, _i, _vp,
                            ctypes.POINTER(_i), _vp],
     "sfseg_enable_iter_timing": [_vp, _i],
@@ -244,6 +245,27 @@ class PowerIteration:
         _check(lib().sfseg_soft_iou_loss(self._h, _ptr(x), _ptr(target), ctypes.byref(loss), _ptr(g), _stream()))
         return loss.value, g
 
+
+    def soft_binarize(self, x: torch.Tensor, radius=(2, 7, 7), sigma=None, iters: int = 5, gain: float = 10.0,
+                      center: float = 0.5, inplace: bool = False):
+        """Soft-binarisation steps (Alg. 1 step 3, sfseg_soft_binarize) from the continuous
+        solution x; returns (soft segmentation in (0, 1), hard mask uint8).  Synchronises."""
+        self._check_volume(x, "x")
+        xo = x if inplace else x.clone()
+        mask = torch.empty((self.T, self.H, self.W), device="cuda", dtype=torch.uint8)
+        _check(lib().sfseg_soft_binarize(self._h, ctypes.byref(neighborhood(radius, sigma)), int(iters), float(gain),
+                                         float(center), _ptr(xo), _ptr(mask), _stream()))
+        return xo, mask
+
+    def segment(self, features: torch.Tensor | None = None, weights=None, bias: float = 0.0, radius=(2, 7, 7),
+                sigma=None, n_iter: int = 60, n_cont: int = 50, gain: float = 10.0, center: float = 0.5,
+                init: str = "uniform", x: torch.Tensor | None = None):
+        """Alg. 1 end to end: n_cont continuous power iterations, then n_iter - n_cont
+        soft-binarisation steps.  Returns (soft segmentation, hard mask)."""
+        if not 0 <= n_cont < n_iter:
+            raise ValueError("need 0 <= n_cont < n_iter")
+        xc = self.power_iterate(features, weights, bias, radius, sigma, n_cont, x=x, init=init)
+        return self.soft_binarize(xc, radius, sigma, n_iter - n_cont, gain, center, inplace=True)
 
     def coarse_start(self, radius=(2, 7, 7), sigma=None, levels: int = 2, tol: float = 1e-4,
                      max_iters: int = 3000, check_every: int = 20):
