@@ -314,7 +314,7 @@ def main():
 
     def step(features, xout):
         h.power_iterate(features, radius=RADIUS, iters=ITERS, x=xout)
-        return h.rayleigh(xout, RADIUS)      # a6: the convergence judge (synchronises)
+        return h.rayleigh(xout, RADIUS)      # Eq. 3 residual check (synchronises)
 
     for _ in range(args.warmup):
         step(feats, x)

@@ -168,7 +168,9 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
     auto stage_f = [&](int frame) -> const TS* {
         return reinterpret_cast<const TS*>(smem + ((frame - tstart) % C::NSTAGE) * C::STAGE_BYTES + C::BOX_BYTES);
     };
+    int next_issue = tstart;         // thread 0: frames [tstart, next_issue) have been requested
     auto issue = [&](int frame) {   // thread 0 only
+        next_issue = frame + 1;
         const int st = (frame - tstart) % C::NSTAGE;
         unsigned char* dst = smem + st * C::STAGE_BYTES;
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -345,10 +347,11 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
     if (!ok) {
         if (tid == 0) {
             atomicOr(P.flags, kFlagTimeout);
-            // let copies still in flight land before the CTA's shared memory goes away
-            for (int i = 0; i < C::NSTAGE; ++i) {
-                for (long long n = 0; n < kSpinLimit; ++n)
-                    if (mbar_try_wait(&bars[i], 0) || mbar_try_wait(&bars[i], 1)) break;
+            // let copies still in flight land before the CTA's shared memory goes away: for each
+            // stage, wait (bounded) for the phase of the last frame requested into it
+            for (int i = 0; i < C::NSTAGE && tstart + i < next_issue; ++i) {
+                const int last = i + ((next_issue - 1 - tstart - i) / C::NSTAGE) * C::NSTAGE;   // relative frame
+                mbar_wait_bounded(&bars[i], (uint32_t)((last / C::NSTAGE) & 1));
             }
         }
         return;

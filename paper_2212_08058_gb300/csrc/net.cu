@@ -1,6 +1,6 @@
 // net.cu -- the learned warm start: a 4-layer 3x3x3 convolutional network that predicts a
 // start vector x0 >= 0 for the power iteration from the raw input channels.  (The paper starts
-// from a uniform vector or from S_m, Alg. 1 line 3; this network is the BASELINE addition.)
+// from a uniform vector or from S_m, Alg. 1 line 3; the network is an addition to the method.)
 //
 //   L1: C_in (<= 16, zero-padded to 16) -> 32, ReLU      L2, L3: 32 -> 32, ReLU
 //   L4: 32 -> 1 (computed as 16 output channels, only the first non-zero), softplus
@@ -68,6 +68,11 @@ __device__ __forceinline__ bool mb_wait(uint64_t* b, uint32_t par, int* flags) {
         if (mb_try(b, par)) return true;
     atomicOr(flags, kFlagTimeout);
     return false;
+}
+// Bounded wait that reports nothing (used after a timeout has already been flagged).
+__device__ __forceinline__ void mb_settle(uint64_t* b, uint32_t par) {
+    for (long long i = 0; i < kSpin; ++i)
+        if (mb_try(b, par)) return;
 }
 __device__ __forceinline__ void tma4(void* dst, const CUtensorMap* m, uint64_t* b, int c0, int c1, int c2, int c3) {
     asm volatile(
@@ -160,6 +165,7 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
     uint64_t* accf = bar + 8;        // [2]
     uint64_t* acce = bar + 10;       // [2]
     uint64_t* wbar = bar + 12;
+    uint64_t* drain = bar + 13;      // completion of this CTA's MMAs, awaited after a timeout
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 16);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -183,6 +189,7 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
             mb_init(&acce[i], 4);
         }
         mb_init(wbar, 1);
+        mb_init(drain, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
@@ -196,6 +203,7 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
+    int issued = 0;                  // producer: input rows requested so far
     if (warp == 0) {
         if (lane == 0) {   // ---------------- producer: weights, then the input rows
             mb_expect(wbar, C::WBYTES);
@@ -203,6 +211,7 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
             for (int i = 0; i < nin; ++i) {
                 const int s = i % NSLOT;
                 if (i >= NSLOT && !mb_wait(&empty[s], (uint32_t)((i / NSLOT - 1) & 1), a.flags)) break;
+                issued = i + 1;
                 mb_expect(&full[s], C::NCH * CHUNK_DATA);
                 unsigned char* dst = ring + s * C::SLOT_BYTES;
                 for (int k = 0; k < C::NCH; ++k) tma4(dst + k * CHUNK_BYTES, &xin, &full[s], 8 * k, w0 - 1, hs - 1 + i, t - 1);
@@ -299,6 +308,21 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
     }
     tc_fence_before();
     __syncthreads();
+    if (*reinterpret_cast<volatile int*>(a.flags) & kFlagTimeout) {
+        // A bounded wait gave up (here or in another CTA): let this CTA's copies and MMAs still
+        // in flight land before its shared memory and TMEM are released.  Each wait is bounded.
+        if (warp == 0 && lane == 0) {
+            mb_settle(wbar, 0);
+            for (int s = 0; s < NSLOT && s < issued; ++s) {
+                const int last = s + ((issued - 1 - s) / NSLOT) * NSLOT;
+                mb_settle(&full[s], (uint32_t)((last / NSLOT) & 1));
+            }
+        } else if (warp == 1 && lane == 0) {
+            umma_commit(drain);      // arrives when every MMA this thread issued has completed
+            mb_settle(drain, 0);
+        }
+        __syncthreads();
+    }
     tc_fence_after();
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");

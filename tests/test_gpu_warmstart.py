@@ -96,3 +96,38 @@ def test_warmstart_entry_point(sf):
         x = h.power_iterate(feats, w, 0.0, (1, 3, 3), iters=5, x=x0.clone(), init="user")
         assert torch.isfinite(x).all()
     net.close()
+
+
+def test_trained_network_gain(sf):
+    """What the trained network adds to the method without it, on generated volumes outside its
+    training and hold-out sets (volume indices 4000+): its refinement of the coarse-to-fine start
+    is closer to the eigenvector (cosine loss) than the coarse start alone, and from it the plain
+    iteration reaches residual 1e-4 in no more steps.  Both beat the uniform start."""
+    from paper_2212_08058_gb300 import warmstart
+    C, T, H, W = 8, 16, 128, 128
+    radius = (2, 7, 7)
+    net = sf.WarmStartNet(C + 1)
+    assert warmstart.load(net), "trained weights missing"
+    w = synth.fixed_weights(C)
+
+    def cos_loss(a, b):
+        return float(1.0 - (a * b).sum() / (a.norm() * b.norm()))
+
+    losses = {"coarse": [], "net": []}
+    its = {"uniform": [], "coarse": [], "net": []}
+    with sf.PowerIteration(C, T, H, W) as h:
+        for i in range(4000, 4006):
+            V = synth.training_volume_torch(i, T, H, W, C).to(torch.bfloat16)
+            label = warmstart.make_label(h, V, w, radius)
+            xc, _ = h.coarse_start(radius, levels=warmstart.COARSE_LEVELS_TRAIN, tol=warmstart.COARSE_TOL)
+            xn = h.warmstart(net, V, xc)
+            losses["coarse"].append(cos_loss(xc, label))
+            losses["net"].append(cos_loss(xn, label))
+            for name, x0, init in (("uniform", torch.empty_like(xc), "uniform"), ("coarse", xc, "user"),
+                                   ("net", xn, "user")):
+                _, n, res, _ = warmstart.iterate_to_residual(h, radius, x0.clone(), 1e-4, chunk=10, init=init)
+                assert res <= 1e-4
+                its[name].append(n)
+    net.close()
+    assert np.mean(losses["net"]) < 0.5 * np.mean(losses["coarse"]), losses
+    assert sum(its["net"]) <= sum(its["coarse"]) < sum(its["uniform"]), its
