@@ -17,6 +17,7 @@ What each function computes, and the passage it follows:
 ``power_filter``              Eq. 7 + Eq. 8 iterated (for volumes too large for a matrix)
 ``soft_binarize``             Alg. 1 step 3 / Sec. 4.1 soft-binarisation iterations and the
                               final hard threshold
+``online``                    Sec. 4.5 partial iterations on sub-windows of a frame stream
 ``rayleigh``                  Eq. 3 Rayleigh quotient and the eigen-residual ||Mx - rho x|| / rho
 ``grad_csr``                  derivative of a loss of x_K w.r.t. the Eq. 9 weights (Sec. 3.4)
 ``soft_iou_loss``             1 - soft-IoU of the max-normalised x against a target mask
@@ -30,7 +31,9 @@ lines of Eq. 6 is "+"; the Eq. 7 filter operator is A = M/alpha; the Gaussian is
 exp(-0.5 sum_a d_a^2 / sigma_a^2), unnormalised, truncated to the box of radii (rt, rh, rw);
 the border is zero padding; every frame is updated each iteration; the soft-binarisation
 sigmoid acts on the new vector scaled to maximum 1, x <- sigmoid(gain (y / max y - center)),
-and the hard segmentation is x > 1/2.
+and the hard segmentation is x > 1/2; the online sub-window of q frames ends at the newest frame,
+its overlap starts from the previous window's final solution and the new frame from the previous
+newest frame's (uniform for the first frame).
 """
 from __future__ import annotations
 
@@ -221,6 +224,28 @@ def soft_binarize(s, f, p: float, alpha: float, radius, x0, K: int, gain: float,
     if rc != 0:
         raise FloatingPointError("max(A x) <= 0 in a soft-binarisation step")
     return x, (x > 0.5).astype(np.uint8)
+
+
+def online(V, w, b: float, p: float, alpha: float, radius, q: int, iters: int, sigma=None):
+    """Sec. 4.5 partial iterations on a stream of frames V [C, T, H, W] (the online form of
+    Alg. 1): when frame k arrives the sub-window is frames k-q+1 .. k (all-zero features before
+    frame 0), started from the previous window's final solution shifted by one frame, with the
+    new frame started from the previous newest frame's solution (uniform at k = 0); then `iters`
+    steps of Eq. 7 + Eq. 8 on the window.  Returns the window solutions, shape [T, q, H, W]
+    (index [k, q-1] is the newest frame's slice after frame k)."""
+    V = _c64(V)
+    C, T, H, W = V.shape
+    f_all = combine(V, w, b)
+    fw = np.zeros((q, H, W))
+    xw = np.zeros((q, H, W))
+    out = np.empty((T, q, H, W))
+    for k in range(T):
+        fw = np.concatenate([fw[1:], f_all[k:k + 1]])
+        newest = xw[-1] if k > 0 else np.ones((H, W))
+        xw = np.concatenate([xw[1:], newest[None]])
+        xw, _ = power_filter(fw, fw, p, alpha, radius, xw, iters, sigma=sigma)
+        out[k] = xw
+    return out
 
 
 def sumsq(x) -> float:

@@ -412,3 +412,46 @@ def test_soft_binarize_gain_limits():
     assert clear.mean() > 0.9
     np.testing.assert_array_equal(mask[clear], (q[clear] > 0.5).astype(np.uint8))
     assert np.all(np.abs(x[clear] - (q[clear] > 0.5)) < 1e-4)
+
+
+# ------------------------------------------------------------------------ Sec. 4.5
+def _dense_top(f, p, alpha, radius, sigma=None):
+    M = oracle.affinity(f, f, p, alpha, radius, sigma).toarray()
+    e, V = scipy.linalg.eigh(M)
+    v = V[:, -1]
+    return (v * np.sign(v.sum())).reshape(f.shape)
+
+
+def test_online_full_window_is_full_video_eigenvector():
+    """q = T: after the last frame the sub-window is the whole video, so enough iterations give
+    the principal eigenvector of the whole video's Eq. 2 matrix (dense LAPACK solver)."""
+    rng = np.random.default_rng(21)
+    V = rng.uniform(0.1, 1.0, size=(1, 4, 5, 6))
+    out = oracle.online(V, None, 0.0, 0.3, 1.0, (1, 2, 2), q=4, iters=600)
+    np.testing.assert_allclose(out[-1], _dense_top(V[0], 0.3, 1.0, (1, 2, 2)), atol=1e-9)
+
+
+def test_online_single_frame_window():
+    """q = 1: each frame is solved alone, so every output is the principal eigenvector of that
+    frame's own 2D matrix."""
+    rng = np.random.default_rng(22)
+    V = rng.uniform(0.1, 1.0, size=(1, 3, 6, 7))
+    out = oracle.online(V, None, 0.0, 0.2, 1.0, (1, 2, 2), q=1, iters=800)
+    for k in range(3):
+        np.testing.assert_allclose(out[k, 0], _dense_top(V[0, k:k + 1], 0.2, 1.0, (1, 2, 2))[0], atol=1e-9)
+
+
+def test_online_start_vectors():
+    """iters = 0 exposes the start vectors: the window holds the previous solution shifted by
+    one frame and the new frame copies the previous newest one, uniform at the first frame, so
+    from an all-uniform history each window is uniform on its min(k+1, q) real frames, zero on
+    the frames before frame 0, normalised to 1."""
+    rng = np.random.default_rng(23)
+    T, q, H, W = 6, 4, 3, 5
+    V = rng.uniform(0.1, 1.0, size=(2, T, H, W))
+    out = oracle.online(V, np.array([0.5, -1.0]), 0.2, 0.3, 1.0, (1, 1, 1), q=q, iters=0)
+    for k in range(T):
+        n = min(k + 1, q)
+        want = np.zeros((q, H, W))
+        want[q - n:] = 1.0 / np.sqrt(n * H * W)
+        np.testing.assert_allclose(out[k], want, rtol=1e-14, atol=0)
