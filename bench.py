@@ -254,6 +254,58 @@ def bench_soft_binarize(sfseg, synth, steps: int = 5, tail: int = 10):
             "foreground_fraction": fg}
 
 
+def bench_separate_maps(sfseg, synth, steps: int = 5):
+    """Separate unary and pairwise maps (Eq. 9 with two channel sets) at the 480p shape: S_m from
+    the crossing-blobs volume, F_m from a second draw of it, radius (2,7,7), 50 iterations,
+    float32.  Device-resident voxel-iterations/s and the iteration kernel's launch time."""
+    import torch
+    Vs = torch.from_numpy(synth.crossing_blobs(T, H, W, seed=SEED)).cuda()
+    Vf = torch.from_numpy(synth.crossing_blobs(T, H, W, seed=SEED + 1)).cuda()
+    h = sfseg.PowerIteration(1, T, H, W)
+    h.set_features_sf(Vs, None, 0.0, Vf)
+    x = torch.empty((T, H, W), device="cuda")
+    for _ in range(2):
+        h.power_iterate(None, radius=RADIUS, iters=ITERS, x=x)
+    torch.cuda.synchronize()
+    h.enable_iter_timing(True)
+    h.iter_timing()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        h.power_iterate(None, radius=RADIUS, iters=ITERS, x=x)
+    e1.record()
+    torch.cuda.synchronize()
+    it_ms, it_n = h.iter_timing()
+    h.close()
+    return {"workload": "separate S_m / F_m maps, C=1 each, fp32 64x480x854, radius (2,7,7), 50 iterations",
+            "value": T * H * W * ITERS * steps / (e0.elapsed_time(e1) * 1e-3), "unit": UNIT,
+            "avg_launch_ms": it_ms / max(it_n, 1)}
+
+
+def bench_online(sfseg, synth, q: int = 13, iters: int = 10, frames: int = 64):
+    """Online form (Sec. 4.5) on the 480p crossing-blobs stream: a 13-frame sub-window (the
+    paper's t = 6 either side of a frame), 10 iterations per incoming frame.  Frames per second
+    and voxel-iterations/s of the window work (CUDA events around the whole stream)."""
+    import torch
+    V = torch.from_numpy(synth.crossing_blobs(T, H, W, seed=SEED)).cuda()
+    frames_in = [V[:, k].contiguous() for k in range(frames)]
+    st = sfseg.OnlineStream(1, q, H, W)
+    for k in range(q):                    # warm-up: fill the window once
+        st.push(frames_in[k], radius=RADIUS, iters=iters)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for k in range(frames):
+        st.push(frames_in[k], radius=RADIUS, iters=iters)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st.close()
+    return {"workload": f"online 480p stream, window {q} frames, {iters} iterations per frame, radius (2,7,7)",
+            "frames_per_s": frames / (ms * 1e-3), "ms_per_frame": ms / frames,
+            "window_voxel_iterations_per_s": frames * q * H * W * iters / (ms * 1e-3)}
+
+
 def bench_time_to_residual(sfseg, synth, warmstart, tol: float = 1e-4):
     """Wall time to the Eq. 3 residual tol on the C = 8 bf16 120 x 1080 x 1920 volume from four
     starts: uniform and S_m with float32 storage (the plain method), the coarse-to-fine start
@@ -403,6 +455,8 @@ def main():
             from paper_2212_08058_gb300 import warmstart
             out["bf16_multichannel"] = bench_bf16_multichannel(sfseg, synth)
             out["soft_binarize"] = bench_soft_binarize(sfseg, synth)
+            out["online"] = bench_online(sfseg, synth)
+            out["separate_maps"] = bench_separate_maps(sfseg, synth)
             out["time_to_residual"] = bench_time_to_residual(sfseg, synth, warmstart)
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()

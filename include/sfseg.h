@@ -97,6 +97,18 @@ int sfseg_destroy(sfseg_handle* h);
 int sfseg_set_features(sfseg_handle* h, const void* features, int dtype, const float* weights,
                        float bias, void* stream);
 
+/* Separate unary and pairwise maps (Eq. 9 with its two channel sets; Alg. 1 lines 1-2):
+ * S_m = sigmoid(sum_i ws_i S_i + bs) from Cs channels (Cs = 1: S_m = S_1, no sigmoid) and F_m
+ * likewise from the handle's C channels (as sfseg_set_features).  Until the next
+ * sfseg_set_features, the iterations use the unary term u = S_m^p and the pairwise term on F_m
+ * (Eq. 7 with s != f), and the S_m start (SFSEG_INIT_SMAP) is S_m.
+ *   s_features: device [Cs][T][H][W] in s_dtype; f_features: device [C][T][H][W] in f_dtype.
+ * Allocates one more float32 volume on first use.  The adjoint (recording) and the coarse start
+ * are for shared maps and return UNSUPPORTED while separate maps are set.  Asynchronous. */
+int sfseg_set_features_sf(sfseg_handle* h, const void* s_features, int s_dtype, int Cs,
+                          const float* s_weights, float s_bias, const void* f_features, int f_dtype,
+                          const float* f_weights, float f_bias, void* stream);
+
 /* Eq. 7 + Eq. 8 (Alg. 1 main loop, continuous iterations): `iters` >= 0 power iterations.
  *   features      device [C][T][H][W] in `dtype`, or NULL to reuse the features already set.
  *   weights/bias  as for sfseg_set_features (used only when features != NULL).
@@ -169,6 +181,34 @@ int sfseg_coarse_start(sfseg_handle* h, const sfseg_neighborhood* nb, int levels
  * previous step left it).  Synchronises (reads the status flags). */
 int sfseg_soft_binarize(sfseg_handle* h, const sfseg_neighborhood* nb, int iters, float gain,
                         float center, float* x_inout, unsigned char* mask_out, void* stream);
+
+/* ------------------------------------------------------------------------------------------
+ * Online form (Sec. 4.5, partial iterations): instead of iterating on the whole video, run a
+ * few iterations on a sub-window of the q most recent frames each time a frame arrives, each
+ * window starting from the previous window's final solution where they overlap.  Reading
+ * taken: the window ends at the newest frame (frames before the first have zero features and
+ * take no part); the overlap starts from the previous solution shifted by one frame, the new
+ * frame from the previous newest frame's solution (uniform for the very first frame).
+ * ---------------------------------------------------------------------------------------- */
+typedef struct sfseg_online sfseg_online;
+
+/* A stream of C-channel frames of H x W with a sub-window of q >= 1 frames.  Allocates a handle
+ * of q frames plus two window solutions (about 7 q H W floats). */
+int sfseg_online_create(const sfseg_params* params, int C, int q, int H, int W, sfseg_online** out);
+int sfseg_online_destroy(sfseg_online* stream_handle);
+
+/* Push the next frame: frame = device [C][H][W] in `dtype`, combined with weights / bias as
+ * sfseg_set_features (Eq. 9); then `iters` power iterations (the first iters_bf16 of them with
+ * bf16 storage) on the window.  x_frame_out: device float32 [H][W] or NULL; receives the
+ * window solution's slice of frame k - lag (lag in [0, q); lag 0 is the frame just pushed, a
+ * larger lag gives a frame that also saw lag later frames).  The slice is part of the
+ * window's unit-norm vector.  Asynchronous. */
+int sfseg_online_push(sfseg_online* stream_handle, const void* frame, int dtype, const float* weights,
+                      float bias, const sfseg_neighborhood* nb, int iters, int iters_bf16, int lag,
+                      float* x_frame_out, void* stream);
+
+/* Copy the current window solution (device float32 [q][H][W], oldest frame first). */
+int sfseg_online_window(sfseg_online* stream_handle, float* x_window_out, void* stream);
 
 /* Learning loss: L = 1 - soft-IoU(xh, g), xh = x / max(x), soft-IoU = sum(xh g) /
  * sum(xh + g - xh g), and dL/dx (the max differentiated at its first argmax).

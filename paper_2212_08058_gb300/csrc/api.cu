@@ -54,6 +54,8 @@ struct sfseg_handle {
     Geom g{};
     int64_t N = 0, NP = 0;            // voxels; elements of an internal (pitched) volume
     float* f32 = nullptr;             // combined features, float32
+    float* s32 = nullptr;             // separate unary map S_m (sfseg_set_features_sf), float32
+    bool sep = false;                 // s32 in use: u = S_m^p instead of f^p
     __nv_bfloat16* fbf = nullptr;     // bf16 copy (allocated on first bf16 use)
     bool fbf_valid = false;
     bool features_set = false;
@@ -148,6 +150,42 @@ static int read_flags(sfseg_handle* h, cudaStream_t s) {
     return SFSEG_OK;
 }
 
+namespace sfseg {
+
+// Shift the combined features one frame towards t = 0 (frame 0 drops out) and combine `frame`
+// (caller layout [C][H][W], `dtype`) into the last frame; used by the online stream.  The
+// shifted copy goes into the idle iterate buffer, which then becomes the feature buffer.
+int handle_push_frame(sfseg_handle* h, const void* frame, int dtype, const float* weights, float bias,
+                      cudaStream_t s) {
+    if (!frame) return fail(SFSEG_ERR_INVALID_ARG, "null frame");
+    if (dtype != SFSEG_F32 && dtype != SFSEG_BF16) return fail(SFSEG_ERR_DTYPE, "dtype must be F32 or BF16");
+    if (h->C > 1 && !weights) return fail(SFSEG_ERR_INVALID_ARG, "C > 1 needs channel weights");
+    if (h->C > 1) {
+        for (int c = 0; c < h->C; ++c)
+            if (!std::isfinite(weights[c])) return fail(SFSEG_ERR_INVALID_ARG, "non-finite channel weight");
+        SFSEG_CUDA(cudaMemcpyAsync(h->wdev, weights, sizeof(float) * h->C, cudaMemcpyHostToDevice, s));
+    }
+    const int64_t frame_elems = (int64_t)h->g.H * h->g.pitch;
+    float* nf = (float*)h->vbuf[0];
+    if (h->g.T > 1)
+        SFSEG_CUDA(cudaMemcpyAsync(nf, h->f32 + frame_elems, sizeof(float) * (size_t)(frame_elems * (h->g.T - 1)),
+                                   cudaMemcpyDeviceToDevice, s));
+    Geom g1 = h->g;
+    g1.T = 1;
+    launch_combine(frame, dtype, h->C, g1, h->wdev, bias, nf + frame_elems * (h->g.T - 1), nullptr, h->flags, s);
+    SFSEG_LAUNCHED();
+    h->vbuf[0] = h->f32;
+    h->f32 = nf;
+    h->fbf_valid = false;
+    h->features_set = true;
+    h->sep = false;
+    h->feat_ptr = nullptr;
+    h->rec_valid = false;
+    return SFSEG_OK;
+}
+
+}  // namespace sfseg
+
 extern "C" {
 
 int sfseg_version(void) { return 100; }
@@ -201,6 +239,7 @@ int sfseg_destroy(sfseg_handle* h) {
     if (!h) return SFSEG_OK;
     cudaDeviceSynchronize();
     cudaFree(h->f32);
+    cudaFree(h->s32);
     cudaFree(h->fbf);
     cudaFree(h->vbuf[0]);
     cudaFree(h->vbuf[1]);
@@ -244,9 +283,35 @@ int sfseg_set_features(sfseg_handle* h, const void* features, int dtype, const f
     SFSEG_LAUNCHED();
     h->fbf_valid = h->fbf != nullptr;
     h->features_set = true;
+    h->sep = false;
     h->feat_ptr = features;
     h->feat_dtype = dtype;
     h->rec_valid = false;
+    return SFSEG_OK;
+}
+
+int sfseg_set_features_sf(sfseg_handle* h, const void* s_features, int s_dtype, int Cs, const float* s_weights,
+                          float s_bias, const void* f_features, int f_dtype, const float* f_weights, float f_bias,
+                          void* stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (!s_features) return fail(SFSEG_ERR_INVALID_ARG, "null s_features");
+    if (s_dtype != SFSEG_F32 && s_dtype != SFSEG_BF16) return fail(SFSEG_ERR_DTYPE, "s_dtype must be F32 or BF16");
+    if (Cs < 1 || Cs > 64) return fail(SFSEG_ERR_INVALID_ARG, "Cs must be in [1, 64]");
+    if (Cs > 1 && !s_weights) return fail(SFSEG_ERR_INVALID_ARG, "Cs > 1 needs unary channel weights");
+    if (Cs > 1)
+        for (int c = 0; c < Cs; ++c)
+            if (!std::isfinite(s_weights[c])) return fail(SFSEG_ERR_INVALID_ARG, "non-finite unary channel weight");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (!h->s32) {
+        SFSEG_CUDA(dalloc(&h->s32, (size_t)h->NP));
+        SFSEG_CUDA(cudaMemsetAsync(h->s32, 0, (size_t)h->NP * sizeof(float), s));
+    }
+    if (int rc = sfseg_set_features(h, f_features, f_dtype, f_weights, f_bias, stream)) return rc;
+    float* swdev = reinterpret_cast<float*>(h->scratch + 32);   // 64 floats of scratch
+    if (Cs > 1) SFSEG_CUDA(cudaMemcpyAsync(swdev, s_weights, sizeof(float) * Cs, cudaMemcpyHostToDevice, s));
+    launch_combine(s_features, s_dtype, Cs, h->g, swdev, s_bias, h->s32, nullptr, h->flags, s);
+    SFSEG_LAUNCHED();
+    h->sep = true;
     return SFSEG_OK;
 }
 
@@ -264,6 +329,8 @@ int sfseg_power_iterate(sfseg_handle* h, const void* features, int dtype, const 
     const int bf = iters_bf16 < 0 ? 0 : (iters_bf16 > iters ? iters : iters_bf16);
     if (record_every > 0 && bf > 0)
         return fail(SFSEG_ERR_UNSUPPORTED, "recording for the adjoint needs float32 iterations");
+    if (record_every > 0 && h->sep && !features)
+        return fail(SFSEG_ERR_UNSUPPORTED, "the adjoint is for shared maps (S = F), not separate ones");
     if (bf > 0 && !h->fbf) {
         SFSEG_CUDA(dalloc(&h->fbf, (size_t)h->NP));
         SFSEG_CUDA(cudaMemsetAsync(h->fbf, 0, (size_t)h->NP * sizeof(__nv_bfloat16), s));
@@ -299,8 +366,9 @@ int sfseg_power_iterate(sfseg_handle* h, const void* features, int dtype, const 
     const float inv_alpha = (float)(1.0 / h->alpha), p = (float)h->p;
     const int vt0 = bf > 0 ? kBF16 : kF32;
     float* last_ckpt = record ? h->ckpt.back() : nullptr;
+    const float* s32 = h->sep ? h->s32 : nullptr;
     launch_prologue(init, x_inout, h->f32, p, h->g, h->vbuf[0], vt0, record ? h->ckpt[0] : nullptr,
-                    iters == 0 ? x_inout : nullptr, acc, s);
+                    iters == 0 ? x_inout : nullptr, acc, s, s32);
     SFSEG_LAUNCHED();
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     if (h->timing && iters > 0) {
@@ -319,7 +387,7 @@ int sfseg_power_iterate(sfseg_handle* h, const void* features, int dtype, const 
             else if ((k + 1) % record_every == 0) ck = h->ckpt[(k + 1) / record_every];
         }
         launch_iterate(h->vbuf[k & 1], vin_t, last ? (void*)x_inout : h->vbuf[(k + 1) & 1], out_t, last, fptr,
-                       vin_t, ck, h->g, tp, inv_alpha, p, acc + k, acc + k + 1, h->flags, s);
+                       vin_t, ck, h->g, tp, inv_alpha, p, acc + k, acc + k + 1, h->flags, s, s32);
         SFSEG_LAUNCHED();
     }
     if (ev1) {
@@ -388,7 +456,7 @@ int sfseg_apply(sfseg_handle* h, const sfseg_neighborhood* nb, const float* x, f
     if (x == y) return fail(SFSEG_ERR_INVALID_ARG, "x and y must not alias");
     if (!h->features_set) return fail(SFSEG_ERR_STATE, "no features set");
     launch_apply_user(x, y, (float*)h->vbuf[1], h->f32, h->g, tp, (float)(1.0 / h->alpha), (float)h->p, h->flags,
-                      (cudaStream_t)stream);
+                      (cudaStream_t)stream, h->sep ? h->s32 : nullptr);
     SFSEG_LAUNCHED();
     return SFSEG_OK;
 }
@@ -404,7 +472,8 @@ int sfseg_rayleigh(sfseg_handle* h, const sfseg_neighborhood* nb, const float* x
     float* y = (float*)h->vbuf[0];
     double* a = h->scratch;
     SFSEG_CUDA(cudaMemsetAsync(a, 0, sizeof(double) * 4, s));
-    launch_apply_user(x, y, (float*)h->vbuf[1], h->f32, h->g, tp, (float)(1.0 / h->alpha), (float)h->p, h->flags, s);
+    launch_apply_user(x, y, (float*)h->vbuf[1], h->f32, h->g, tp, (float)(1.0 / h->alpha), (float)h->p, h->flags, s,
+                      h->sep ? h->s32 : nullptr);
     launch_dot2(x, y, h->N, a, s);
     launch_resid(x, y, h->N, a, s);
     SFSEG_LAUNCHED();
@@ -489,6 +558,7 @@ int sfseg_coarse_start(sfseg_handle* h, const sfseg_neighborhood* nb, int levels
     if (!(tol > 0.0) || max_iters < 1 || check_every < 1)
         return fail(SFSEG_ERR_INVALID_ARG, "tol > 0, max_iters >= 1 and check_every >= 1 are required");
     if (!h->features_set) return fail(SFSEG_ERR_STATE, "no features set");
+    if (h->sep) return fail(SFSEG_ERR_UNSUPPORTED, "the coarse start is for shared maps (S = F)");
     cudaStream_t s = (cudaStream_t)stream;
     // (re)build the pyramid when its depth or shape does not match
     if ((int)h->lvl.size() != levels) {
@@ -591,16 +661,17 @@ int sfseg_soft_binarize(sfseg_handle* h, const sfseg_neighborhood* nb, int iters
     float* v = (float*)h->vbuf[1];                     // u * x, internal layout
     unsigned* key = reinterpret_cast<unsigned*>(h->scratch + 60);
     const bool fast = fast_iterate_supported(tp);
+    const float* s32 = h->sep ? h->s32 : nullptr;
     for (int k = 0; k < iters; ++k) {
         const bool last = k == iters - 1;
         if (k == 0 || !fast)
-            launch_apply_user(x_inout, y, v, h->f32, h->g, tp, inv_alpha, p, h->flags, s);
+            launch_apply_user(x_inout, y, v, h->f32, h->g, tp, inv_alpha, p, h->flags, s, s32);
         else if (!launch_iterate_fast(v, kF32, y, kF32, true, h->f32, h->g, tp, inv_alpha, p, nullptr, nullptr,
-                                      h->flags, s))
+                                      h->flags, s, s32))
             return fail(SFSEG_ERR_CUDA, "stencil launch failed");
         launch_max_key(y, h->N, key, s);
         launch_sigmoid_step(y, key, gain, center, h->f32, p, h->g, x_inout, (fast && !last) ? v : nullptr,
-                            last ? mask_out : nullptr, h->flags, s);
+                            last ? mask_out : nullptr, h->flags, s, s32);
         SFSEG_LAUNCHED();
     }
     return read_flags(h, s);

@@ -135,9 +135,12 @@ struct Params {
     int* flags;
     void* out;        // next state (internal pitch) or x~ (caller layout)
     const void* f;    // f in global memory (internal pitch), read by the epilogue
+    const float* s;   // separate unary map S_m (float32, internal pitch; SEP kernels only)
 };
 
-template <int RT, int RH, int RW, typename TS, typename TVO, bool OUT_X>
+// SEP: the unary term u = s^p comes from a separate map S_m (Eq. 9 with its own channels)
+// instead of from f.
+template <int RT, int RH, int RW, typename TS, typename TVO, bool OUT_X, bool SEP>
 __global__ void __launch_bounds__(NTHR, SFSEG_FAST_MINB)
 iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtensorMap mf, Params P) {
     using C = Cfg<RT, RH, RW, TS, TVO, OUT_X>;
@@ -216,14 +219,25 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
         // behind the two spatial passes.  Outside the volume f is taken as 0, so those
         // positions give x~ = 0 and add nothing to the norm (row padding is not relied on).
         float2 fo[4];
+        float2 so[SEP ? 4 : 1];
 #pragma unroll
         for (int m = 0; m < 4; ++m) fo[m] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int m = 0; m < (SEP ? 4 : 1); ++m) so[m] = make_float2(0.f, 0.f);
         if (to >= t0 && h < g.H && wr < TH) {
             const TS* fg = reinterpret_cast<const TS*>(P.f) + ((int64_t)to * g.H + h) * g.pitch + wbase;
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 if (wbase + 2 * m + 1 < g.W) fo[m] = ld_pair(fg + 2 * m);
                 else if (wbase + 2 * m < g.W) fo[m].x = ldf(fg + 2 * m);
+            }
+            if constexpr (SEP) {
+                const float* sg = P.s + ((int64_t)to * g.H + h) * g.pitch + wbase;
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    if (wbase + 2 * m + 1 < g.W) so[m] = ld_pair(sg + 2 * m);
+                    else if (wbase + 2 * m < g.W) so[m].x = sg[2 * m];
+                }
             }
         }
         const uint32_t parity = (uint32_t)(((tt - tstart) / C::NSTAGE) & 1);
@@ -305,7 +319,8 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 const float2 fv = fo[m];
-                const float2 u = make_float2(unary_pow_fast(fv.x, P.p), unary_pow_fast(fv.y, P.p));
+                const float2 sv = SEP ? so[SEP ? m : 0] : fv;
+                const float2 u = make_float2(unary_pow_fast(sv.x, P.p), unary_pow_fast(sv.y, P.p));
                 const float2 e = fma2(make_float2(-fv.x, -fv.y), fv, f2(P.inv_alpha));   // 1/alpha - f^2
                 float2 B = fma2(e, y[0][m], make_float2(-y[1][m].x, -y[1][m].y));
                 B = fma2(mul2(f2(2.f), fv), y[2][m], B);
@@ -411,14 +426,15 @@ static int pick_chunk(int T, int tiles, int slots, int rt) {
     return best;
 }
 
-template <int RT, int RH, int RW, typename TS, typename TVO, bool OUT_X>
+template <int RT, int RH, int RW, typename TS, typename TVO, bool OUT_X, bool SEP = false>
 static bool launch_t(const void* vin, void* out, const void* f, const Geom& g, const Taps& tp, float inv_alpha,
-                     float p, const double* acc_in, double* acc_out, int* flags, cudaStream_t s) {
+                     float p, const double* acc_in, double* acc_out, int* flags, cudaStream_t s,
+                     const float* s32 = nullptr) {
     using C = Cfg<RT, RH, RW, TS, TVO, OUT_X>;
     constexpr bool bf = sizeof(TS) == 2;
     CUtensorMap mv, mf;
     if (!make_map(&mv, vin, bf, g, C::BH) || !make_map(&mf, f, bf, g, C::BH)) return false;
-    auto kern = iter_fast<RT, RH, RW, TS, TVO, OUT_X>;
+    auto kern = iter_fast<RT, RH, RW, TS, TVO, OUT_X, SEP>;
     static int slots_per_sm = -1;
     if (slots_per_sm < 0) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess) return false;
@@ -434,6 +450,7 @@ static bool launch_t(const void* vin, void* out, const void* f, const Geom& g, c
     for (int i = 0; i < 2 * kMaxRH + 1; ++i) P.gh[i] = make_float2(tp.gh[i], tp.gh[i]);
     for (int i = 0; i < 2 * kMaxRW + 1; ++i) P.gw[i] = make_float2(tp.gw[i], tp.gw[i]);
     P.f = f;
+    P.s = s32;
     const int tx = (g.W + TW - 1) / TW, ty = (g.H + TH - 1) / TH;
     P.tchunk = pick_chunk(g.T, tx * ty, slots_per_sm * num_sms(), RT);
     P.acc_in = acc_in;
@@ -449,8 +466,13 @@ static bool launch_t(const void* vin, void* out, const void* f, const Geom& g, c
 template <int RT, int RH, int RW>
 static bool dispatch(const void* vin, int vin_type, void* out, int out_type, bool out_x, const void* f,
                      const Geom& g, const Taps& tp, float ia, float p, const double* ai, double* ao, int* fl,
-                     cudaStream_t s) {
+                     cudaStream_t s, const float* s32) {
     using bf = __nv_bfloat16;
+    if (s32) {   // separate unary map: float32 storage only (the generic stencil serves bf16)
+        if (vin_type != kF32) return false;
+        if (out_x) return launch_t<RT, RH, RW, float, float, true, true>(vin, out, f, g, tp, ia, p, ai, ao, fl, s, s32);
+        return launch_t<RT, RH, RW, float, float, false, true>(vin, out, f, g, tp, ia, p, ai, ao, fl, s, s32);
+    }
     if (vin_type == kF32) {
         if (out_x) return launch_t<RT, RH, RW, float, float, true>(vin, out, f, g, tp, ia, p, ai, ao, fl, s);
         return launch_t<RT, RH, RW, float, float, false>(vin, out, f, g, tp, ia, p, ai, ao, fl, s);
@@ -475,11 +497,11 @@ bool fast_iterate_supported(const Taps& tp) {
 
 bool launch_iterate_fast(const void* vin, int vin_type, void* out, int out_type, bool out_x, const void* f,
                          const Geom& g, const Taps& tp, float inv_alpha, float p, const double* acc_in,
-                         double* acc_out, int* flags, cudaStream_t s) {
+                         double* acc_out, int* flags, cudaStream_t s, const float* s32) {
 #define SFSEG_GO(A, B, C)                                                                                   \
     if (tp.rt == A && tp.rh == B && tp.rw == C)                                                             \
         return fast::dispatch<A, B, C>(vin, vin_type, out, out_type, out_x, f, g, tp, inv_alpha, p, acc_in, \
-                                       acc_out, flags, s);
+                                       acc_out, flags, s, s32);
     SFSEG_FAST_RADII(SFSEG_GO)
 #undef SFSEG_GO
     return false;

@@ -33,6 +33,7 @@ struct OpIter {
     TVO* out;
     int out_pitch;
     float* ckpt;
+    const float* sm;   // separate unary map (nullable: s = f)
     Geom g;
     float inv_alpha, p, s;
 
@@ -51,7 +52,7 @@ struct OpIter {
                                         float&) const {
         const int64_t i = ((int64_t)t * g.H + h) * g.pitch + w;
         const float fv = ldf(f + i);
-        const float u = unary_pow(fv, p);
+        const float u = unary_pow(sm ? sm[i] : fv, p);
         const float B = (inv_alpha - fv * fv) * c[0] - c[1] + 2.f * fv * c[2];
         const float xt = s * u * B;
         acc0 += xt * xt;
@@ -69,6 +70,7 @@ struct OpApply {
     const float* f;
     float* out;
     int out_pitch;
+    const float* sm;   // separate unary map (nullable: s = f)
     Geom g;
     float inv_alpha, p, s;
 
@@ -77,8 +79,9 @@ struct OpApply {
     }
     __device__ __forceinline__ void load(int t, int h, int w, float (&z)[NS]) const {
         const float xv = x[((int64_t)t * g.H + h) * x_pitch + w];
-        const float fv = f[((int64_t)t * g.H + h) * g.pitch + w];
-        const float z1 = unary_pow(fv, p) * xv;
+        const int64_t j = ((int64_t)t * g.H + h) * g.pitch + w;
+        const float fv = f[j];
+        const float z1 = unary_pow(sm ? sm[j] : fv, p) * xv;
         const float z3 = fv * z1;
         z[0] = z1;
         z[1] = fv * z3;
@@ -86,8 +89,9 @@ struct OpApply {
     }
     __device__ __forceinline__ void epi(int t, int h, int w, const float (&c)[NS], float& acc0,
                                         float&) const {
-        const float fv = f[((int64_t)t * g.H + h) * g.pitch + w];
-        const float u = unary_pow(fv, p);
+        const int64_t j = ((int64_t)t * g.H + h) * g.pitch + w;
+        const float fv = f[j];
+        const float u = unary_pow(sm ? sm[j] : fv, p);
         const float y = s * u * ((inv_alpha - fv * fv) * c[0] - c[1] + 2.f * fv * c[2]);
         acc0 += y * y;
         out[((int64_t)t * g.H + h) * out_pitch + w] = y;
@@ -112,8 +116,9 @@ int num_sms() {
 template <typename TVI, typename TVO, typename TF, bool OUT_X>
 static void iterate_t(const void* vin, void* out, const void* f, float* ckpt, Geom g, const Taps& tp,
                       float inv_alpha, float p, const double* acc_in, double* acc_out, int* flags,
-                      cudaStream_t s) {
+                      cudaStream_t s, const float* s32) {
     OpIter<TVI, TVO, TF, OUT_X> op;
+    op.sm = s32;
     op.v = (const TVI*)vin;
     op.f = (const TF*)f;
     op.out = (TVO*)out;
@@ -128,14 +133,15 @@ static void iterate_t(const void* vin, void* out, const void* f, float* ckpt, Ge
 
 void launch_iterate(const void* vin, int vin_type, void* out, int out_type, bool out_x, const void* f,
                     int f_type, float* ckpt, Geom g, const Taps& tp, float inv_alpha, float p,
-                    const double* acc_in, double* acc_out, int* flags, cudaStream_t s) {
+                    const double* acc_in, double* acc_out, int* flags, cudaStream_t s, const float* s32) {
     using bf = __nv_bfloat16;
     // The TMA kernel serves the method's radii; recording checkpoints uses the generic one.
     if (ckpt == nullptr && fast_iterate_supported(tp) &&
-        launch_iterate_fast(vin, vin_type, out, out_type, out_x, f, g, tp, inv_alpha, p, acc_in, acc_out, flags, s))
+        launch_iterate_fast(vin, vin_type, out, out_type, out_x, f, g, tp, inv_alpha, p, acc_in, acc_out, flags, s,
+                            s32))
         return;
 #define SFSEG_IT(TVI, TVO, TF, OX) \
-    iterate_t<TVI, TVO, TF, OX>(vin, out, f, ckpt, g, tp, inv_alpha, p, acc_in, acc_out, flags, s)
+    iterate_t<TVI, TVO, TF, OX>(vin, out, f, ckpt, g, tp, inv_alpha, p, acc_in, acc_out, flags, s, s32)
     // A step of the bf16 phase reads v and f in bf16 and writes bf16, or float32 when the next
     // step (or the caller's x) is float32; a float32 step reads and writes float32.
     (void)f_type;
@@ -152,8 +158,9 @@ void launch_iterate(const void* vin, int vin_type, void* out, int out_type, bool
 
 void launch_apply(const float* x, int x_pitch, float* y, int y_pitch, const float* f32, Geom g,
                   const Taps& tp, float inv_alpha, float p, const double* acc_in, double* acc_out,
-                  int* flags, cudaStream_t s) {
+                  int* flags, cudaStream_t s, const float* s32) {
     OpApply op;
+    op.sm = s32;
     op.x = x;
     op.x_pitch = x_pitch;
     op.f = f32;
@@ -167,29 +174,30 @@ void launch_apply(const float* x, int x_pitch, float* y, int y_pitch, const floa
 }
 
 // v = u x from a caller-layout x into the internal layout (the state the iteration kernels read).
-__global__ void to_state_kernel(const float* x, const float* f32, float p, Geom g, float* v) {
+__global__ void to_state_kernel(const float* x, const float* f32, const float* s32, float p, Geom g, float* v) {
     const int64_t HW = (int64_t)g.H * g.W, N = HW * g.T;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
         const int64_t t = i / HW, rem = i - t * HW;
         const int64_t h = rem / g.W, wc = rem - h * g.W;
         const int64_t j = (t * g.H + h) * g.pitch + wc;
-        v[j] = unary_pow(f32[j], p) * x[i];
+        v[j] = unary_pow(s32 ? s32[j] : f32[j], p) * x[i];
     }
 }
 
 void launch_apply_user(const float* x, float* y, float* scratch_v, const float* f32, Geom g, const Taps& tp,
-                       float inv_alpha, float p, int* flags, cudaStream_t s) {
+                       float inv_alpha, float p, int* flags, cudaStream_t s, const float* s32) {
     if (fast_iterate_supported(tp)) {
         const int64_t N = (int64_t)g.T * g.H * g.W;
         int blocks = (int)((N + 255) / 256);
         if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
-        to_state_kernel<<<blocks, 256, 0, s>>>(x, f32, p, g, scratch_v);
+        to_state_kernel<<<blocks, 256, 0, s>>>(x, f32, s32, p, g, scratch_v);
         count_launches(1);
         // one unscaled step (no norm input) that writes x~ = A x into the caller's layout
-        if (launch_iterate_fast(scratch_v, kF32, y, kF32, true, f32, g, tp, inv_alpha, p, nullptr, nullptr, flags, s))
+        if (launch_iterate_fast(scratch_v, kF32, y, kF32, true, f32, g, tp, inv_alpha, p, nullptr, nullptr, flags, s,
+                                s32))
             return;
     }
-    launch_apply(x, g.W, y, g.W, f32, g, tp, inv_alpha, p, nullptr, nullptr, flags, s);
+    launch_apply(x, g.W, y, g.W, f32, g, tp, inv_alpha, p, nullptr, nullptr, flags, s, s32);
 }
 
 // -------------------------------------------------------------------------- Eq. 9 combine
@@ -233,8 +241,8 @@ void launch_combine(const void* feat, int feat_dtype, int C, Geom g, const float
 
 // ------------------------------------------------------------------------- start vector
 template <typename TV>
-__global__ void prologue_kernel(int init, const float* x_user, const float* f32, float p, Geom g, TV* v0,
-                                float* x_copy, float* x_user_out, double* acc0) {
+__global__ void prologue_kernel(int init, const float* x_user, const float* f32, const float* s32, float p, Geom g,
+                                TV* v0, float* x_copy, float* x_user_out, double* acc0) {
     const int64_t HW = (int64_t)g.H * g.W, N = HW * g.T;
     float part = 0.f;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
@@ -242,10 +250,10 @@ __global__ void prologue_kernel(int init, const float* x_user, const float* f32,
         const int64_t t = i / HW, rem = i - t * HW;
         const int64_t h = rem / g.W, wc = rem - h * g.W;
         const int64_t j = (t * g.H + h) * g.pitch + wc;
-        const float fv = f32[j];
-        const float x = init == 0 ? x_user[i] : (init == 1 ? 1.f : fv);
+        const float sv = s32 ? s32[j] : f32[j];
+        const float x = init == 0 ? x_user[i] : (init == 1 ? 1.f : sv);
         part += x * x;
-        stf(v0 + j, unary_pow(fv, p) * x);
+        stf(v0 + j, unary_pow(sv, p) * x);
         if (x_copy) x_copy[j] = x;
         if (x_user_out) x_user_out[i] = x;
     }
@@ -254,15 +262,16 @@ __global__ void prologue_kernel(int init, const float* x_user, const float* f32,
 }
 
 void launch_prologue(int init, const float* x_user, const float* f32, float p, Geom g, void* v0, int vtype,
-                     float* x_copy, float* x_user_out, double* acc0, cudaStream_t s) {
+                     float* x_copy, float* x_user_out, double* acc0, cudaStream_t s, const float* s32) {
     const int64_t N = (int64_t)g.T * g.H * g.W;
     int blocks = (int)((N + 255) / 256);
     if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
     if (vtype == kF32)
-        prologue_kernel<float><<<blocks, 256, 0, s>>>(init, x_user, f32, p, g, (float*)v0, x_copy, x_user_out, acc0);
+        prologue_kernel<float><<<blocks, 256, 0, s>>>(init, x_user, f32, s32, p, g, (float*)v0, x_copy, x_user_out,
+                                                      acc0);
     else
-        prologue_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(init, x_user, f32, p, g, (__nv_bfloat16*)v0, x_copy,
-                                                              x_user_out, acc0);
+        prologue_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(init, x_user, f32, s32, p, g, (__nv_bfloat16*)v0,
+                                                              x_copy, x_user_out, acc0);
     count_launches(1);
 }
 

@@ -34,7 +34,8 @@ __global__ void max_key_kernel(const float* y, int64_t n, unsigned* key) {
 // x = sigmoid(gain (y / max y - center)) for the N voxels (caller layout).  Optional outputs:
 // v (internal layout, u * x, the next stencil input) and mask (x > 1/2 as 0/1 bytes).
 __global__ void sigmoid_step_kernel(const float* y, const unsigned* key, float gain, float center, const float* f32,
-                                    float p, Geom g, float* x, float* v, unsigned char* mask, int* flags) {
+                                    const float* s32, float p, Geom g, float* x, float* v, unsigned char* mask,
+                                    int* flags) {
     const float m = order_value(*key);
     if (!(m > 0.f) || isinf(m)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(flags, m > 0.f ? kFlagNonfinite : kFlagZeroNorm);
@@ -49,7 +50,7 @@ __global__ void sigmoid_step_kernel(const float* y, const unsigned* key, float g
             const int64_t t = i / HW, rem = i - t * HW;
             const int64_t h = rem / g.W, w = rem - h * g.W;
             const int64_t j = (t * g.H + h) * g.pitch + w;
-            v[j] = unary_pow(f32[j], p) * xi;
+            v[j] = unary_pow(s32 ? s32[j] : f32[j], p) * xi;
         }
     }
 }
@@ -67,9 +68,10 @@ void launch_max_key(const float* y, int64_t n, unsigned* key, cudaStream_t s) {
 }
 
 void launch_sigmoid_step(const float* y, const unsigned* key, float gain, float center, const float* f32, float p,
-                         Geom g, float* x, float* v, unsigned char* mask, int* flags, cudaStream_t s) {
-    sigmoid_step_kernel<<<grid_for((int64_t)g.T * g.H * g.W), 256, 0, s>>>(y, key, gain, center, f32, p, g, x, v,
-                                                                          mask, flags);
+                         Geom g, float* x, float* v, unsigned char* mask, int* flags, cudaStream_t s,
+                         const float* s32) {
+    sigmoid_step_kernel<<<grid_for((int64_t)g.T * g.H * g.W), 256, 0, s>>>(y, key, gain, center, f32, s32, p, g, x,
+                                                                          v, mask, flags);
     count_launches(1);
 }
 

@@ -7,6 +7,8 @@
 
 #include "common.cuh"
 
+struct sfseg_handle;
+
 namespace sfseg {
 
 enum StoreType { kF32 = 0, kBF16 = 1 };
@@ -19,8 +21,10 @@ void launch_combine(const void* feat, int feat_dtype, int C, Geom g, const float
 // Start vector (Alg. 1 line 3 or uniform or the caller's x): writes v0 = u x0 (internal, in
 // `vtype`), acc[0] = ||x0||^2, and optionally an FP32 copy of x0 (internal pitch) and x0 into
 // the caller's layout.
+// With separate unary maps (s32 != nullptr, internal layout) u = s^p and the S_m start is s.
 void launch_prologue(int init, const float* x_user, const float* f32, float p, Geom g, void* v0,
-                     int vtype, float* x_copy, float* x_user_out, double* acc0, cudaStream_t s);
+                     int vtype, float* x_copy, float* x_user_out, double* acc0, cudaStream_t s,
+                     const float* s32 = nullptr);
 
 // One Eq. 7 power-iteration step in the scaled, u-weighted form (see kernels_generic.cu):
 // input v_k = u x~_k (internal), output v_{k+1} = u x~_{k+1} or, when `out_x`, x~_{k+1} itself
@@ -29,20 +33,20 @@ void launch_prologue(int init, const float* x_user, const float* f32, float p, G
 void launch_iterate(const void* vin, int vin_type, void* out, int out_type, bool out_x,
                     const void* f, int f_type, float* ckpt, Geom g, const Taps& tp,
                     float inv_alpha, float p, const double* acc_in, double* acc_out, int* flags,
-                    cudaStream_t s);
+                    cudaStream_t s, const float* s32 = nullptr);
 
 // TMA-staged step for the radii (1,3,3) and (2,7,7) (kernels_fast.cu).  Returns false when the
 // radius is not one of them or a tensor map cannot be encoded; nothing is launched then.
 bool fast_iterate_supported(const Taps& tp);
 bool launch_iterate_fast(const void* vin, int vin_type, void* out, int out_type, bool out_x, const void* f,
                          const Geom& g, const Taps& tp, float inv_alpha, float p, const double* acc_in,
-                         double* acc_out, int* flags, cudaStream_t s);
+                         double* acc_out, int* flags, cudaStream_t s, const float* s32 = nullptr);
 
 // y = s * A x in the plain (x-space) form: x with pitch x_pitch, y with pitch y_pitch, FP32
 // features; s = 1/sqrt(*acc_in) (or 1 if acc_in is null); acc_out += ||y||^2 (nullable).
 void launch_apply(const float* x, int x_pitch, float* y, int y_pitch, const float* f32, Geom g,
                   const Taps& tp, float inv_alpha, float p, const double* acc_in, double* acc_out,
-                  int* flags, cudaStream_t s);
+                  int* flags, cudaStream_t s, const float* s32 = nullptr);
 
 // bf16 copy of a float32 array (n elements).
 void launch_to_bf16(const float* a, __nv_bfloat16* b, int64_t n, cudaStream_t s);
@@ -50,7 +54,7 @@ void launch_to_bf16(const float* a, __nv_bfloat16* b, int64_t n, cudaStream_t s)
 // y = A x for caller-layout x and y (FP32); scratch_v holds one internal-layout volume.  Uses
 // the TMA kernel for the radii it serves, the generic stencil otherwise.
 void launch_apply_user(const float* x, float* y, float* scratch_v, const float* f32, Geom g, const Taps& tp,
-                       float inv_alpha, float p, int* flags, cudaStream_t s);
+                       float inv_alpha, float p, int* flags, cudaStream_t s, const float* s32 = nullptr);
 
 // Restriction of f (internal layout) by (pt, ph, pw) into a caller-layout coarse volume, and
 // trilinear prolongation of a caller-layout coarse x (kernels_multilevel.cu).
@@ -65,7 +69,13 @@ void launch_scale_by_max(float* x, int64_t n, unsigned* key, cudaStream_t s);
 // optional v = u * x (internal layout) and mask = (x > 1/2).
 void launch_max_key(const float* y, int64_t n, unsigned* key, cudaStream_t s);
 void launch_sigmoid_step(const float* y, const unsigned* key, float gain, float center, const float* f32, float p,
-                         Geom g, float* x, float* v, unsigned char* mask, int* flags, cudaStream_t s);
+                         Geom g, float* x, float* v, unsigned char* mask, int* flags, cudaStream_t s,
+                         const float* s32 = nullptr);
+
+// Online stream support (api.cu): shift the handle's combined features one frame towards t = 0
+// and combine a caller-layout frame [C][H][W] into the last frame.
+int handle_push_frame(sfseg_handle* h, const void* frame, int dtype, const float* weights, float bias,
+                      cudaStream_t s);
 
 // x *= 1/sqrt(*acc) over a caller-layout volume.
 void launch_scale_inv_norm(float* x, int64_t n, const double* acc, int* flags, cudaStream_t s);

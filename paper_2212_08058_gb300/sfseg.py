@@ -58,7 +58,12 @@ SIGNATURES = {
     "sfseg_rayleigh": [_vp, ctypes.POINTER(Neighborhood), _vp, _dp, _dp, _vp],
     "sfseg_backward": [_vp, ctypes.POINTER(Neighborhood), _vp, _fp, _fp, _vp],
     "sfseg_soft_iou_loss": [_vp, _vp, _vp, _dp, _vp, _vp],
+    "sfseg_set_features_sf": [_vp, _vp, _i, _i, _fp, _f, _vp, _i, _fp, _f, _vp],
     "sfseg_soft_binarize": [_vp, ctypes.POINTER(Neighborhood), _i, _f, _f, _vp, _vp, _vp],
+    "sfseg_online_create": [ctypes.POINTER(Params), _i, _i, _i, _i, ctypes.POINTER(_vp)],
+    "sfseg_online_destroy": [_vp],
+    "sfseg_online_push": [_vp, _vp, _i, _fp, _f, ctypes.POINTER(Neighborhood), _i, _i, _i, _vp, _vp],
+    "sfseg_online_window": [_vp, _vp, _vp],
     "sfseg_coarse_start": [_vp, ctypes.POINTER(Neighborhood), _i, ctypes.c_double, _i, _i, _vp,
                            ctypes.POINTER(_i), _vp],
     "sfseg_enable_iter_timing": [_vp, _i],
@@ -187,6 +192,22 @@ class PowerIteration:
                                         _stream()))
         self._features = features
 
+    def set_features_sf(self, s_features: torch.Tensor, s_weights, s_bias: float, f_features: torch.Tensor,
+                        f_weights=None, f_bias: float = 0.0):
+        """Separate unary and pairwise maps (sfseg_set_features_sf): s_features [Cs, T, H, W],
+        f_features [C, T, H, W]."""
+        self._check_features(f_features)
+        if (not s_features.is_cuda or not s_features.is_contiguous() or s_features.dim() != 4
+                or tuple(s_features.shape[1:]) != (self.T, self.H, self.W)):
+            raise ValueError("s_features must be a contiguous CUDA tensor [Cs, T, H, W]")
+        Cs = s_features.shape[0]
+        _, swp = _host_floats(s_weights, Cs)
+        _, fwp = _host_floats(f_weights, self.C)
+        _check(lib().sfseg_set_features_sf(self._h, _ptr(s_features), _dtype_code(s_features), int(Cs), swp,
+                                           float(s_bias), _ptr(f_features), _dtype_code(f_features), fwp,
+                                           float(f_bias), _stream()))
+        self._features = f_features
+
     def power_iterate(self, features: torch.Tensor | None = None, weights=None, bias: float = 0.0,
                       radius=(2, 7, 7), sigma=None, iters: int = 50, iters_bf16: int = 0,
                       x: torch.Tensor | None = None, init: str = "uniform", record_every: int = 0,
@@ -296,6 +317,51 @@ class PowerIteration:
         n = ctypes.c_int64()
         _check(lib().sfseg_iter_timing(self._h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
+
+
+class OnlineStream:
+    """Partial iterations on a stream of frames (Sec. 4.5; sfseg_online_*): a sub-window of the
+    q most recent frames, re-solved with a few iterations whenever a frame arrives."""
+
+    def __init__(self, C: int, q: int, H: int, W: int, alpha: float = 1.0, p: float = 0.1):
+        self.C, self.q, self.H, self.W = C, q, H, W
+        o = ctypes.c_void_p()
+        _check(lib().sfseg_online_create(ctypes.byref(Params(alpha, p)), C, q, H, W, ctypes.byref(o)))
+        self._o = o
+
+    def close(self):
+        if getattr(self, "_o", None):
+            lib().sfseg_online_destroy(self._o)
+            self._o = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def push(self, frame: torch.Tensor, weights=None, bias: float = 0.0, radius=(2, 7, 7), sigma=None,
+             iters: int = 5, iters_bf16: int = 0, lag: int = 0) -> torch.Tensor:
+        """Push frame [C, H, W]; returns the window solution's slice of frame k - lag [H, W]."""
+        if not frame.is_cuda or not frame.is_contiguous() or tuple(frame.shape) != (self.C, self.H, self.W):
+            raise ValueError(f"frame must be a contiguous CUDA tensor of shape {(self.C, self.H, self.W)}")
+        _, wp = _host_floats(weights, self.C)
+        out = torch.empty((self.H, self.W), device="cuda", dtype=torch.float32)
+        _check(lib().sfseg_online_push(self._o, _ptr(frame), _dtype_code(frame), wp, float(bias),
+                                       ctypes.byref(neighborhood(radius, sigma)), int(iters), int(iters_bf16),
+                                       int(lag), _ptr(out), _stream()))
+        return out
+
+    def window(self) -> torch.Tensor:
+        out = torch.empty((self.q, self.H, self.W), device="cuda", dtype=torch.float32)
+        _check(lib().sfseg_online_window(self._o, _ptr(out), _stream()))
+        return out
 
 
 class WarmStartNet:
