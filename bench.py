@@ -254,6 +254,34 @@ def bench_soft_binarize(sfseg, synth, steps: int = 5, tail: int = 10):
             "foreground_fraction": fg}
 
 
+def bench_r133_storage(sfseg, synth, steps: int = 10):
+    """Radius (1,3,3) (3 x 7 x 7, the neighbourhood of the paper's Sec. 4.2 counts) on the 480p
+    crossing-blobs volume, 50 iterations, float32 storage against bf16 storage.  At this radius
+    the step needs 51 FMA per 12 bytes (float32), so bytes matter: CUDA-event launch time and the
+    fraction of the measured HBM peak for each storage type."""
+    import torch
+    V = torch.from_numpy(synth.crossing_blobs(T, H, W, seed=SEED)).cuda()
+    h = sfseg.PowerIteration(1, T, H, W)
+    h.set_features(V)
+    x = torch.empty((T, H, W), device="cuda")
+    out = {"workload": "plain SFSeg 480p C=1, radius (1,3,3), 50 iterations"}
+    for name, nb, bytes_per in (("f32", 0, 12.0), ("bf16", ITERS, 6.0)):
+        for _ in range(2):
+            h.power_iterate(None, radius=(1, 3, 3), iters=ITERS, iters_bf16=nb, x=x)
+        torch.cuda.synchronize()
+        h.enable_iter_timing(True)
+        h.iter_timing()
+        for _ in range(steps):
+            h.power_iterate(None, radius=(1, 3, 3), iters=ITERS, iters_bf16=nb, x=x)
+        ms, n = h.iter_timing()
+        h.enable_iter_timing(False)
+        per = ms / max(n, 1)
+        out[name] = {"avg_launch_ms": per, "voxel_iterations_per_s": T * H * W / (per * 1e-3),
+                     "hbm_frac_of_measured": bytes_per * T * H * W / (per * 1e-3) / 1e9 / _peaks()[0]}
+    h.close()
+    return out
+
+
 def bench_separate_maps(sfseg, synth, steps: int = 5):
     """Separate unary and pairwise maps (Eq. 9 with two channel sets) at the 480p shape: S_m from
     the crossing-blobs volume, F_m from a second draw of it, radius (2,7,7), 50 iterations,
@@ -457,6 +485,7 @@ def main():
             out["soft_binarize"] = bench_soft_binarize(sfseg, synth)
             out["online"] = bench_online(sfseg, synth)
             out["separate_maps"] = bench_separate_maps(sfseg, synth)
+            out["r133_storage"] = bench_r133_storage(sfseg, synth)
             out["time_to_residual"] = bench_time_to_residual(sfseg, synth, warmstart)
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()

@@ -112,7 +112,8 @@ def load(net: sfseg.WarmStartNet, path: str = DEFAULT_WEIGHTS) -> bool:
 
 
 def compare_starts(feats: torch.Tensor, w, radius=(2, 7, 7), tol: float = 1e-4, net=None, chunk: int = 20,
-                   max_iters: int = 4000, bf16_until: float = 2e-3, levels: int = 2):
+                   max_iters: int = 4000, bf16_until: float = 2e-3, levels: int = 2, coarse_tol: float = COARSE_TOL,
+                   kinds=("uniform", "smap", "coarse", "net")):
     """Wall time (CUDA events around the whole run: coarse solves, the network and every residual
     check included) to reach residual <= tol on the volume from
       uniform_f32       the uniform start, float32 storage (the plain method),
@@ -131,6 +132,7 @@ def compare_starts(feats: torch.Tensor, w, radius=(2, 7, 7), tol: float = 1e-4, 
         runs = [("uniform_f32", "uniform", None), ("smap_f32", "smap", None), ("coarse_f32", "coarse", None)]
         if net is not None:
             runs.append(("warmstart_bf16", "net", bf16_until))
+        runs = [r for r in runs if r[1] in kinds]
         for name, kind, b16 in runs:
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -138,7 +140,7 @@ def compare_starts(feats: torch.Tensor, w, radius=(2, 7, 7), tol: float = 1e-4, 
             coarse_its = None
             init = "user"
             if kind in ("coarse", "net"):
-                x, coarse_its = h.coarse_start(radius, levels=levels, tol=COARSE_TOL)
+                x, coarse_its = h.coarse_start(radius, levels=levels, tol=coarse_tol)
                 if kind == "net":
                     x = h.warmstart(net, feats, x)
             else:
