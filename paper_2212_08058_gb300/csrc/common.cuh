@@ -43,9 +43,14 @@ __device__ __forceinline__ float unary_pow(float s, float p) {
     return s > 0.f ? exp2f(p * log2f(s)) : 0.f;
 }
 
-// Faster variant through the SFU approximations (relative error ~1e-7 for p <= 1).
+// Faster variant on the special-function unit: u = 2^(p log2 s) with the approximate log2 and
+// exp2 instructions (relative error a few 1e-7 for p <= 1).  s = 0 gives log2 s = -inf and
+// u = +0, so no branch is needed (s < 0 never reaches here: features are checked >= 0).
 __device__ __forceinline__ float unary_pow_fast(float s, float p) {
-    return s > 0.f ? exp2f(p * __log2f(s)) : 0.f;
+    float l, u;
+    asm("lg2.approx.f32 %0, %1;" : "=f"(l) : "f"(s));
+    asm("ex2.approx.f32 %0, %1;" : "=f"(u) : "f"(p * l));
+    return u;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {

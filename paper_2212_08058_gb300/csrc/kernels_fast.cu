@@ -190,6 +190,15 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
     const int hcp = C::CP_LO + tid % C::NCP;                // h-pass column pair
     const int hseg = tid / C::NCP;                          // h-pass row segment
 
+    // the filter taps, copied once from the kernel parameters (measured ~1-2 % faster than reading
+    // the parameter bank at every use)
+    float2 ghr[2 * RH + 1], gwr[2 * RW + 1], gtr[2 * RT + 1];
+#pragma unroll
+    for (int d = 0; d <= 2 * RH; ++d) ghr[d] = P.gh[d];
+#pragma unroll
+    for (int d = 0; d <= 2 * RW; ++d) gwr[d] = P.gw[d];
+#pragma unroll
+    for (int d = 0; d <= 2 * RT; ++d) gtr[d] = P.gt[d];
     // t-filter in transposed direct form: for each of the 3 signals and 4 column pairs the
     // 2rt running partial sums of the 2rt+1-tap filter; with x[n] the w-filtered frame n and
     // g_j = gt[2rt - j], the output y[n] = sum_j g_j x[n - j] is the t-filtered frame n - rt.
@@ -261,7 +270,7 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
                 for (int o = 0; o < RHS; ++o) {
                     const int d = j - o;
                     if (d >= 0 && d <= 2 * RH) {
-                        const float2 gd = P.gh[d];
+                        const float2 gd = ghr[d];
                         acc[o][0] = fma2(v, gd, acc[o][0]);
                         acc[o][1] = fma2(z2, gd, acc[o][1]);
                         acc[o][2] = fma2(z3, gd, acc[o][2]);
@@ -295,7 +304,7 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
                 for (int m = 0; m < 4; ++m) acc[0][m] = acc[1][m] = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int d = 0; d <= 2 * RW; ++d) {
-                    const float2 gd = P.gw[d];
+                    const float2 gd = gwr[d];
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
                         const int q = 2 * m + d + C::ODD;
@@ -306,10 +315,10 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
                     const float2 x = __fadd2_rn(acc[0][m], acc[1][m]);
-                    y[k][m] = fma2(x, P.gt[2 * RT], st[0][k][m]);
+                    y[k][m] = fma2(x, gtr[2 * RT], st[0][k][m]);
 #pragma unroll
-                    for (int j = 0; j < 2 * RT - 1; ++j) st[j][k][m] = fma2(x, P.gt[2 * RT - 1 - j], st[j + 1][k][m]);
-                    st[2 * RT - 1][k][m] = mul2(x, P.gt[0]);
+                    for (int j = 0; j < 2 * RT - 1; ++j) st[j][k][m] = fma2(x, gtr[2 * RT - 1 - j], st[j + 1][k][m]);
+                    st[2 * RT - 1][k][m] = mul2(x, gtr[0]);
                 }
             }
         }
