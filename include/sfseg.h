@@ -266,6 +266,15 @@ int sfseg_net_adamw(sfseg_net* net, float lr, float beta1, float beta2, float ep
 int sfseg_warmstart(sfseg_handle* h, sfseg_net* net, const void* features, int dtype,
                     const float* x_coarse, float* x0_out, void* stream);
 
+/* Self-test of failure reporting (no counterpart in the paper).  Every wait inside this
+ * library's kernels (for a TMA copy or an MMA to complete) is bounded: on expiry the kernel
+ * raises a timeout flag, lets its own copies in flight land (again bounded), releases what it
+ * holds and returns, and the host call returns SFSEG_ERR_TIMEOUT.  This call runs that path on
+ * purpose: a one-warp kernel waits `spins` times (1 <= spins <= 1e6) on a barrier that nothing
+ * completes.  Returns SFSEG_ERR_TIMEOUT -- the expected outcome -- and leaves the handle and the
+ * CUDA context usable.  Synchronises. */
+int sfseg_selftest_wait(sfseg_handle* h, long long spins, void* stream);
+
 /* Instrumentation (no counterpart in the paper).  When enabled, each sfseg_power_iterate call
  * records two CUDA events on its stream, before its first and after its last iteration-kernel
  * launch.  sfseg_iter_timing waits for the recorded events, returns the summed milliseconds and

@@ -677,6 +677,15 @@ int sfseg_soft_binarize(sfseg_handle* h, const sfseg_neighborhood* nb, int iters
     return read_flags(h, s);
 }
 
+int sfseg_selftest_wait(sfseg_handle* h, long long spins, void* stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (spins < 1 || spins > 1000000) return fail(SFSEG_ERR_INVALID_ARG, "spins must be in [1, 1e6]");
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_wait_probe(spins, h->flags, s);
+    SFSEG_LAUNCHED();
+    return read_flags(h, s);
+}
+
 int sfseg_soft_iou_loss(sfseg_handle* h, const float* x, const float* target, double* loss, float* grad_x,
                         void* stream) {
     if (int rc = check_handle(h)) return rc;

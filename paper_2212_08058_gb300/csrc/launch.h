@@ -77,6 +77,10 @@ void launch_sigmoid_step(const float* y, const unsigned* key, float gain, float 
 int handle_push_frame(sfseg_handle* h, const void* frame, int dtype, const float* weights, float bias,
                       cudaStream_t s);
 
+// Bounded-wait self-test (selftest.cu): waits `spins` times on an mbarrier nothing completes,
+// then raises kFlagTimeout.
+void launch_wait_probe(long long spins, int* flags, cudaStream_t s);
+
 // x *= 1/sqrt(*acc) over a caller-layout volume.
 void launch_scale_inv_norm(float* x, int64_t n, const double* acc, int* flags, cudaStream_t s);
 

@@ -66,6 +66,7 @@ SIGNATURES = {
     "sfseg_online_window": [_vp, _vp, _vp],
     "sfseg_coarse_start": [_vp, ctypes.POINTER(Neighborhood), _i, ctypes.c_double, _i, _i, _vp,
                            ctypes.POINTER(_i), _vp],
+    "sfseg_selftest_wait": [_vp, ctypes.c_longlong, _vp],
     "sfseg_enable_iter_timing": [_vp, _i],
     "sfseg_iter_timing": [_vp, _dp, ctypes.POINTER(ctypes.c_int64)],
     "sfseg_kernel_launches": [ctypes.POINTER(ctypes.c_int64)],
@@ -307,6 +308,11 @@ class PowerIteration:
         _check(lib().sfseg_warmstart(self._h, net._n, _ptr(features), _dtype_code(features), _ptr(x_coarse),
                                      _ptr(x0), _stream()))
         return x0
+
+    def selftest_wait(self, spins: int = 1000):
+        """Run the bounded-wait failure path on purpose (sfseg_selftest_wait); raises SFSegError
+        with status TIMEOUT, which is the expected outcome."""
+        _check(lib().sfseg_selftest_wait(self._h, int(spins), _stream()))
 
     def enable_iter_timing(self, on: bool = True):
         _check(lib().sfseg_enable_iter_timing(self._h, int(bool(on))))

@@ -263,3 +263,19 @@ def test_full_size_sfsegpp_bf16_parity():
     xo, nuo = _oracle(V, (2, 7, 7), K, weights=w)
     assert np.abs(xg - xo).max() <= TOL_BF16
     np.testing.assert_allclose(nug, nuo, rtol=2e-3)
+
+
+def test_bounded_wait_reports_timeout():
+    """The failure path of the kernels' bounded waits, run on purpose without a GPU fault: a
+    wait on a barrier nothing completes gives up, the call returns TIMEOUT, and the handle and
+    the context keep working (the next power iteration matches the oracle)."""
+    sf = _sf()
+    V = synth.drifting_blob(4, 32, 40, seed=7500)
+    with sf.PowerIteration(1, 4, 32, 40) as h:
+        for _ in range(2):
+            with pytest.raises(sf.SFSegError) as e:
+                h.selftest_wait(200)
+            assert e.value.status == "TIMEOUT"
+        x = h.power_iterate(torch.from_numpy(V).cuda(), radius=(1, 3, 3), iters=8).cpu().numpy()
+    xo, _ = _oracle(V, (1, 3, 3), 8)
+    assert np.abs(x - xo).max() <= TOL_F32
