@@ -20,6 +20,7 @@
 #include "common.cuh"
 #include "launch.h"
 #include "stencil.cuh"
+#include "voxels.cuh"
 
 namespace sfseg {
 
@@ -175,22 +176,14 @@ void launch_apply(const float* x, int x_pitch, float* y, int y_pitch, const floa
 
 // v = u x from a caller-layout x into the internal layout (the state the iteration kernels read).
 __global__ void to_state_kernel(const float* x, const float* f32, const float* s32, float p, Geom g, float* v) {
-    const int64_t HW = (int64_t)g.H * g.W, N = HW * g.T;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = i / HW, rem = i - t * HW;
-        const int64_t h = rem / g.W, wc = rem - h * g.W;
-        const int64_t j = (t * g.H + h) * g.pitch + wc;
-        v[j] = unary_pow(s32 ? s32[j] : f32[j], p) * x[i];
-    }
+    for_each_voxel(g, [&](int64_t i, int64_t j) { v[j] = unary_pow_fast(s32 ? s32[j] : f32[j], p) * x[i]; });
 }
 
 void launch_apply_user(const float* x, float* y, float* scratch_v, const float* f32, Geom g, const Taps& tp,
                        float inv_alpha, float p, int* flags, cudaStream_t s, const float* s32) {
     if (fast_iterate_supported(tp)) {
-        const int64_t N = (int64_t)g.T * g.H * g.W;
-        int blocks = (int)((N + 255) / 256);
-        if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
-        to_state_kernel<<<blocks, 256, 0, s>>>(x, f32, s32, p, g, scratch_v);
+        const RowLaunch rl = row_launch(g, num_sms());
+        to_state_kernel<<<rl.blocks, rl.threads, 0, s>>>(x, f32, s32, p, g, scratch_v);
         count_launches(1);
         // one unscaled step (no norm input) that writes x~ = A x into the caller's layout
         if (launch_iterate_fast(scratch_v, kF32, y, kF32, true, f32, g, tp, inv_alpha, p, nullptr, nullptr, flags, s,
@@ -204,10 +197,9 @@ void launch_apply_user(const float* x, float* y, float* scratch_v, const float* 
 template <typename TIn>
 __global__ void combine_kernel(const TIn* feat, int C, Geom g, const float* w, float bias, float* f32,
                                __nv_bfloat16* fbf, int* flags) {
-    const int64_t HW = (int64_t)g.H * g.W, N = HW * g.T;
+    const int64_t N = (int64_t)g.H * g.W * g.T;
     int bad = 0;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x) {
+    for_each_voxel(g, [&](int64_t i, int64_t j) {
         float fv;
         if (C == 1) {
             fv = ldf(feat + i);
@@ -217,25 +209,21 @@ __global__ void combine_kernel(const TIn* feat, int C, Geom g, const float* w, f
             fv = 1.f / (1.f + expf(-z));
         }
         if (!(fv >= 0.f) || isinf(fv)) bad = 1;
-        const int64_t t = i / HW, rem = i - t * HW;
-        const int64_t h = rem / g.W, wc = rem - h * g.W;
-        const int64_t j = (t * g.H + h) * g.pitch + wc;
         f32[j] = fv;
         if (fbf) fbf[j] = __float2bfloat16_rn(fv);
-    }
+    });
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, kFlagBadFeature);
 }
 
 void launch_combine(const void* feat, int feat_dtype, int C, Geom g, const float* w_dev, float bias,
                     float* f32, __nv_bfloat16* fbf, int* flags, cudaStream_t s) {
-    const int64_t N = (int64_t)g.T * g.H * g.W;
-    int blocks = (int)((N + 255) / 256);
-    if (blocks > 16 * num_sms()) blocks = 16 * num_sms();
+    const RowLaunch rl = row_launch(g, num_sms());
     if (feat_dtype == kF32)
-        combine_kernel<float><<<blocks, 256, 0, s>>>((const float*)feat, C, g, w_dev, bias, f32, fbf, flags);
+        combine_kernel<float><<<rl.blocks, rl.threads, 0, s>>>((const float*)feat, C, g, w_dev, bias, f32, fbf,
+                                                               flags);
     else
-        combine_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>((const __nv_bfloat16*)feat, C, g, w_dev, bias,
-                                                             f32, fbf, flags);
+        combine_kernel<__nv_bfloat16><<<rl.blocks, rl.threads, 0, s>>>((const __nv_bfloat16*)feat, C, g, w_dev,
+                                                                       bias, f32, fbf, flags);
     count_launches(1);
 }
 
@@ -243,35 +231,28 @@ void launch_combine(const void* feat, int feat_dtype, int C, Geom g, const float
 template <typename TV>
 __global__ void prologue_kernel(int init, const float* x_user, const float* f32, const float* s32, float p, Geom g,
                                 TV* v0, float* x_copy, float* x_user_out, double* acc0) {
-    const int64_t HW = (int64_t)g.H * g.W, N = HW * g.T;
     float part = 0.f;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t t = i / HW, rem = i - t * HW;
-        const int64_t h = rem / g.W, wc = rem - h * g.W;
-        const int64_t j = (t * g.H + h) * g.pitch + wc;
+    for_each_voxel(g, [&](int64_t i, int64_t j) {
         const float sv = s32 ? s32[j] : f32[j];
         const float x = init == 0 ? x_user[i] : (init == 1 ? 1.f : sv);
         part += x * x;
-        stf(v0 + j, unary_pow(sv, p) * x);
+        stf(v0 + j, unary_pow_fast(sv, p) * x);
         if (x_copy) x_copy[j] = x;
         if (x_user_out) x_user_out[i] = x;
-    }
+    });
     const double b = block_sum((double)part);
     if (threadIdx.x == 0) atomicAdd(acc0, b);
 }
 
 void launch_prologue(int init, const float* x_user, const float* f32, float p, Geom g, void* v0, int vtype,
                      float* x_copy, float* x_user_out, double* acc0, cudaStream_t s, const float* s32) {
-    const int64_t N = (int64_t)g.T * g.H * g.W;
-    int blocks = (int)((N + 255) / 256);
-    if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
+    const RowLaunch rl = row_launch(g, num_sms(), 8);
     if (vtype == kF32)
-        prologue_kernel<float><<<blocks, 256, 0, s>>>(init, x_user, f32, s32, p, g, (float*)v0, x_copy, x_user_out,
-                                                      acc0);
+        prologue_kernel<float><<<rl.blocks, rl.threads, 0, s>>>(init, x_user, f32, s32, p, g, (float*)v0, x_copy,
+                                                                x_user_out, acc0);
     else
-        prologue_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(init, x_user, f32, s32, p, g, (__nv_bfloat16*)v0,
-                                                              x_copy, x_user_out, acc0);
+        prologue_kernel<__nv_bfloat16><<<rl.blocks, rl.threads, 0, s>>>(init, x_user, f32, s32, p, g,
+                                                                        (__nv_bfloat16*)v0, x_copy, x_user_out, acc0);
     count_launches(1);
 }
 

@@ -13,30 +13,31 @@
 namespace sfseg {
 
 // out[Tc][Hc][Wc] = mean of f over the (pt x ph x pw) block that lies inside the volume.
-// f in the internal layout of `g`; out in caller layout (pitch Wc).
+// f in the internal layout of `g`; out in caller layout (pitch Wc).  Rows (tc, hc) over the
+// blocks, columns over the threads.
 __global__ void pool_f_kernel(const float* f, Geom g, int pt, int ph, int pw, int Tc, int Hc, int Wc, float* out) {
-    const int64_t N = (int64_t)Tc * Hc * Wc;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const int tc = (int)(i / ((int64_t)Hc * Wc));
-        const int hc = (int)((i / Wc) % Hc);
-        const int wc = (int)(i % Wc);
-        float s = 0.f;
-        int n = 0;
-        for (int a = 0; a < pt; ++a) {
-            const int t = tc * pt + a;
-            if (t >= g.T) continue;
-            for (int b = 0; b < ph; ++b) {
-                const int h = hc * ph + b;
-                if (h >= g.H) continue;
-                for (int c = 0; c < pw; ++c) {
-                    const int w = wc * pw + c;
-                    if (w >= g.W) continue;
-                    s += f[((int64_t)t * g.H + h) * g.pitch + w];
-                    ++n;
+    const int64_t rows = (int64_t)Tc * Hc;
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int tc = (int)(row / Hc), hc = (int)(row - (int64_t)tc * Hc);
+        for (int wc = threadIdx.x; wc < Wc; wc += blockDim.x) {
+            float s = 0.f;
+            int n = 0;
+            for (int a = 0; a < pt; ++a) {
+                const int t = tc * pt + a;
+                if (t >= g.T) continue;
+                for (int b = 0; b < ph; ++b) {
+                    const int h = hc * ph + b;
+                    if (h >= g.H) continue;
+                    for (int c = 0; c < pw; ++c) {
+                        const int w = wc * pw + c;
+                        if (w >= g.W) continue;
+                        s += f[((int64_t)t * g.H + h) * g.pitch + w];
+                        ++n;
+                    }
                 }
             }
+            out[row * Wc + wc] = n ? s / (float)n : 0.f;
         }
-        out[i] = n ? s / (float)n : 0.f;
     }
 }
 
@@ -55,27 +56,33 @@ __device__ __forceinline__ void lin(int d, int p, int nc, int& i0, int& i1, floa
     w1 = src - (float)i0;
 }
 
-// x[T][H][W] (caller layout) = trilinear interpolation of xc[Tc][Hc][Wc].
+// x[T][H][W] (caller layout) = trilinear interpolation of xc[Tc][Hc][Wc].  Rows (t, h) over
+// the blocks (their t and h weights computed once per row), columns over the threads.
 __global__ void upsample_kernel(const float* xc, int Tc, int Hc, int Wc, int pt, int ph, int pw, int T, int H, int W,
                                 float* x) {
-    const int64_t N = (int64_t)T * H * W;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const int t = (int)(i / ((int64_t)H * W));
-        const int h = (int)((i / W) % H);
-        const int w = (int)(i % W);
-        int t0, t1, h0, h1, w0, w1i;
-        float at, ah, aw;
+    const int64_t rows = (int64_t)T * H;
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int t = (int)(row / H), h = (int)(row - (int64_t)t * H);
+        int t0, t1, h0, h1;
+        float at, ah;
         lin(t, pt, Tc, t0, t1, at);
         lin(h, ph, Hc, h0, h1, ah);
-        lin(w, pw, Wc, w0, w1i, aw);
-        auto X = [&](int a, int b, int c) { return xc[((int64_t)a * Hc + b) * Wc + c]; };
-        const float c00 = X(t0, h0, w0) + aw * (X(t0, h0, w1i) - X(t0, h0, w0));
-        const float c01 = X(t0, h1, w0) + aw * (X(t0, h1, w1i) - X(t0, h1, w0));
-        const float c10 = X(t1, h0, w0) + aw * (X(t1, h0, w1i) - X(t1, h0, w0));
-        const float c11 = X(t1, h1, w0) + aw * (X(t1, h1, w1i) - X(t1, h1, w0));
-        const float c0 = c00 + ah * (c01 - c00);
-        const float c1 = c10 + ah * (c11 - c10);
-        x[i] = c0 + at * (c1 - c0);
+        const float* r00 = xc + ((int64_t)t0 * Hc + h0) * Wc;
+        const float* r01 = xc + ((int64_t)t0 * Hc + h1) * Wc;
+        const float* r10 = xc + ((int64_t)t1 * Hc + h0) * Wc;
+        const float* r11 = xc + ((int64_t)t1 * Hc + h1) * Wc;
+        for (int w = threadIdx.x; w < W; w += blockDim.x) {
+            int w0, w1i;
+            float aw;
+            lin(w, pw, Wc, w0, w1i, aw);
+            const float c00 = r00[w0] + aw * (r00[w1i] - r00[w0]);
+            const float c01 = r01[w0] + aw * (r01[w1i] - r01[w0]);
+            const float c10 = r10[w0] + aw * (r10[w1i] - r10[w0]);
+            const float c11 = r11[w0] + aw * (r11[w1i] - r11[w0]);
+            const float c0 = c00 + ah * (c01 - c00);
+            const float c1 = c10 + ah * (c11 - c10);
+            x[row * W + w] = c0 + at * (c1 - c0);
+        }
     }
 }
 
@@ -95,14 +102,20 @@ static int grid_for(int64_t n) {
     return (int)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
+static int row_threads(int w) { return w >= 256 ? 256 : ((w + 31) / 32) * 32; }
+static int row_blocks(int64_t rows) {
+    const int64_t cap = 16 * (int64_t)num_sms();
+    return (int)(rows < cap ? (rows > 0 ? rows : 1) : cap);
+}
+
 void launch_pool_f(const float* f, Geom g, int pt, int ph, int pw, int Tc, int Hc, int Wc, float* out, cudaStream_t s) {
-    pool_f_kernel<<<grid_for((int64_t)Tc * Hc * Wc), 256, 0, s>>>(f, g, pt, ph, pw, Tc, Hc, Wc, out);
+    pool_f_kernel<<<row_blocks((int64_t)Tc * Hc), row_threads(Wc), 0, s>>>(f, g, pt, ph, pw, Tc, Hc, Wc, out);
     count_launches(1);
 }
 
 void launch_upsample(const float* xc, int Tc, int Hc, int Wc, int pt, int ph, int pw, int T, int H, int W, float* x,
                      cudaStream_t s) {
-    upsample_kernel<<<grid_for((int64_t)T * H * W), 256, 0, s>>>(xc, Tc, Hc, Wc, pt, ph, pw, T, H, W, x);
+    upsample_kernel<<<row_blocks((int64_t)T * H), row_threads(W), 0, s>>>(xc, Tc, Hc, Wc, pt, ph, pw, T, H, W, x);
     count_launches(1);
 }
 

@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "launch.h"
 #include "order_key.cuh"
+#include "voxels.cuh"
 
 namespace sfseg {
 
@@ -41,18 +42,13 @@ __global__ void sigmoid_step_kernel(const float* y, const unsigned* key, float g
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(flags, m > 0.f ? kFlagNonfinite : kFlagZeroNorm);
         return;
     }
-    const int64_t HW = (int64_t)g.H * g.W, N = HW * g.T;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-        const float xi = 1.f / (1.f + expf(-gain * (y[i] / m - center)));
+    const float gm = -gain;
+    for_each_voxel(g, [&](int64_t i, int64_t j) {
+        const float xi = 1.f / (1.f + expf(gm * (y[i] / m - center)));
         x[i] = xi;
         if (mask) mask[i] = xi > 0.5f ? 1 : 0;
-        if (v) {
-            const int64_t t = i / HW, rem = i - t * HW;
-            const int64_t h = rem / g.W, w = rem - h * g.W;
-            const int64_t j = (t * g.H + h) * g.pitch + w;
-            v[j] = unary_pow(s32 ? s32[j] : f32[j], p) * xi;
-        }
-    }
+        if (v) v[j] = unary_pow_fast(s32 ? s32[j] : f32[j], p) * xi;
+    });
 }
 
 static int grid_for(int64_t n) {
@@ -70,8 +66,8 @@ void launch_max_key(const float* y, int64_t n, unsigned* key, cudaStream_t s) {
 void launch_sigmoid_step(const float* y, const unsigned* key, float gain, float center, const float* f32, float p,
                          Geom g, float* x, float* v, unsigned char* mask, int* flags, cudaStream_t s,
                          const float* s32) {
-    sigmoid_step_kernel<<<grid_for((int64_t)g.T * g.H * g.W), 256, 0, s>>>(y, key, gain, center, f32, s32, p, g, x,
-                                                                          v, mask, flags);
+    const RowLaunch rl = row_launch(g, num_sms());
+    sigmoid_step_kernel<<<rl.blocks, rl.threads, 0, s>>>(y, key, gain, center, f32, s32, p, g, x, v, mask, flags);
     count_launches(1);
 }
 

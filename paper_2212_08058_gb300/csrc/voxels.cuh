@@ -1,0 +1,33 @@
+// voxels.cuh -- the visiting order of the element-wise kernels: rows (t, h) over the grid's
+// blocks, columns w over a block's threads, so that neighbouring threads touch neighbouring
+// addresses and no thread divides an index to find its row.
+#pragma once
+
+#include "common.cuh"
+
+namespace sfseg {
+
+// f(i, j) for every voxel: i its index in the caller's layout [T][H][W], j in the internal
+// pitched layout [T][H][pitch].
+template <typename F>
+__device__ __forceinline__ void for_each_voxel(const Geom& g, F&& f) {
+    const int64_t rows = (int64_t)g.T * g.H;
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int64_t i0 = row * g.W, j0 = row * g.pitch;
+        for (int w = threadIdx.x; w < g.W; w += blockDim.x) f(i0 + w, j0 + w);
+    }
+}
+
+// Launch shape for for_each_voxel: up to 256 threads (a multiple of 32 covering W when W is
+// small), at most `per_sm` blocks per SM.
+struct RowLaunch {
+    int blocks, threads;
+};
+inline RowLaunch row_launch(const Geom& g, int sms, int per_sm = 16) {
+    const int64_t rows = (int64_t)g.T * g.H;
+    int threads = g.W >= 256 ? 256 : ((g.W + 31) / 32) * 32;
+    int64_t b = rows < (int64_t)per_sm * sms ? rows : (int64_t)per_sm * sms;
+    return {(int)(b > 0 ? b : 1), threads > 0 ? threads : 32};
+}
+
+}  // namespace sfseg
