@@ -158,8 +158,9 @@ int sfseg_backward(sfseg_handle* h, const sfseg_neighborhood* nb, const float* g
  * has nearly the same principal eigenvector at those scales at an eighth of the cost per
  * iteration.  The coarsest of `levels` (1..4) levels is solved from the uniform start, each
  * finer level from the trilinear upsampling of the coarser solution, each until the Eq. 3
- * residual of its own operator is <= tol (checked every `check_every` iterations, at most
- * `max_iters` per level); the finest coarse solution, upsampled to the handle's volume and
+ * residual of its own operator is <= tol (checked after `check_every` iterations, then where
+ * the residual's geometric rate over the last two checks predicts tol, at most 8 check_every
+ * iterations later; at most `max_iters` per level); the finest coarse solution, upsampled to the handle's volume and
  * scaled to maximum 1, is written to x0_out (device float32 [T][H][W]) for SFSEG_INIT_USER.  iters_out: host array of
  * `levels` ints (iterations per level, index 0 = finest coarse level) or NULL.  Requires the
  * features set; allocates the pyramid (about 1/7 of the handle's workspace) on first use.

@@ -622,16 +622,27 @@ int sfseg_coarse_start(sfseg_handle* h, const sfseg_neighborhood* nb, int levels
             SFSEG_LAUNCHED();
             init = SFSEG_INIT_USER;
         }
-        int its = 0;
-        double res = 1e300;
+        int its = 0, step = check_every, last_its = -1;
+        double res = 1e300, last_res = 0.0;
         while (its < max_iters && res > tol) {
-            const int k = std::min(check_every, max_iters - its);
+            const int k = std::min(step, max_iters - its);
             if (int rc = sfseg_power_iterate(c, nullptr, 0, nullptr, 0.f, &nbs[(size_t)l], k, 0, h->lvl_x[l], init, 0,
                                              nullptr, stream))
                 return rc;
             init = SFSEG_INIT_USER;
             its += k;
             if (int rc = sfseg_rayleigh(c, &nbs[(size_t)l], h->lvl_x[l], nullptr, &res, stream)) return rc;
+            // next check where the residual's geometric rate over the last two checks predicts
+            // tol (a multiple of 10 iterations, between check_every and 8 check_every away)
+            step = check_every;
+            if (last_its >= 0 && res > tol && res > 0.0 && res < last_res) {
+                const double rate = std::log(res / last_res) / (double)(its - last_its);
+                const double need = std::log(tol / res) / rate;
+                const double r10 = std::ceil(need / 10.0) * 10.0;
+                step = (int)std::min(std::max(r10, (double)check_every), 8.0 * check_every);
+            }
+            last_its = its;
+            last_res = res;
         }
         if (iters_out) iters_out[l] = its;
     }

@@ -35,8 +35,9 @@ void launch_iterate(const void* vin, int vin_type, void* out, int out_type, bool
                     float inv_alpha, float p, const double* acc_in, double* acc_out, int* flags,
                     cudaStream_t s, const float* s32 = nullptr);
 
-// TMA-staged step for the radii (1,3,3) and (2,7,7) (kernels_fast.cu).  Returns false when the
-// radius is not one of them or a tensor map cannot be encoded; nothing is launched then.
+// TMA-staged step for the radii (1,3,3), (2,7,7), (1,4,4) and (1,2,2) (kernels_fast.cu).  s32
+// (nullable): a separate unary map (float32 storage only).  Returns false when the radius has no
+// compiled kernel or a tensor map cannot be encoded; nothing is launched then.
 bool fast_iterate_supported(const Taps& tp);
 bool launch_iterate_fast(const void* vin, int vin_type, void* out, int out_type, bool out_x, const void* f,
                          const Geom& g, const Taps& tp, float inv_alpha, float p, const double* acc_in,
