@@ -161,9 +161,33 @@ def cpu_baseline(seconds_budget: float = 20.0):
     oracle.power_filter(f, f, 0.1, 1.0, RADIUS, start, k)
     dt = time.perf_counter() - t0
     nvox = T * H * W
-    return {"value": nvox * k / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-            "sample": f"{k} of the {ITERS} iterations of the full {T}x{H}x{W} volume, FP64 filter form, "
-                      f"{dt:.1f} s"}
+    out = {"value": nvox * k / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": f"{k} of the {ITERS} iterations of the full {T}x{H}x{W} volume, FP64 filter form, "
+                     f"{dt:.1f} s"}
+    # the same filter form on one core (one iteration of an 8-frame slab), and the explicit
+    # sparse-matrix form at the small 8 x 64 x 64 drifting-blob case (4.2 M non-zeros)
+    threads = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        slab = f[:8]
+        t0 = time.perf_counter()
+        oracle.power_filter(slab, slab, 0.1, 1.0, RADIUS, np.ones(slab.shape), 1)
+        dt1 = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(threads)
+    out["single_core"] = {"value": slab.size / dt1, "unit": UNIT,
+                          "sample": f"one iteration of an 8x{H}x{W} slab, FP64 filter form, {dt1:.1f} s"}
+    fb = synth.drifting_blob(8, 64, 64, seed=1000)[0].astype(np.float64)
+    t0 = time.perf_counter()
+    M = oracle.affinity(fb, fb, 0.1, 1.0, (1, 3, 3))
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.power_csr(M, np.ones(fb.size), 20)
+    t_iter = time.perf_counter() - t0
+    out["csr_small"] = {"value": fb.size * 20 / t_iter, "unit": UNIT, "nnz": int(M.nnz),
+                        "build_s": t_build, "cores": threads,
+                        "sample": "explicit Eq. 2 matrix of the 8x64x64 drifting blob, radius (1,3,3), 20 iterations"}
+    return out
 
 
 def run_reference(args, rank, world):
