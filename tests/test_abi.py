@@ -60,6 +60,15 @@ def test_argument_checks_without_gpu(libpath):
     assert L.sfseg_destroy(None) == 0
     nb = sfseg.neighborhood((1, 3, 3))
     assert L.sfseg_power_iterate(None, None, 0, None, 0.0, ctypes.byref(nb), 1, 0, None, 1, 0, None, None) == 1
+    # the other entry points refuse a null handle before touching the GPU
+    assert L.sfseg_soft_binarize(None, ctypes.byref(nb), 1, 1.0, 0.5, None, None, None) == 1
+    assert L.sfseg_set_features_sf(None, None, 0, 1, None, 0.0, None, 0, None, 0.0, None) == 1
+    assert L.sfseg_coarse_start(None, ctypes.byref(nb), 2, 1e-4, 10, 10, None, None, None) == 1
+    assert L.sfseg_selftest_wait(None, 10, None) == 1
+    o = ctypes.c_void_p()
+    assert L.sfseg_online_create(ctypes.byref(ok), 1, 0, 8, 8, ctypes.byref(o)) == 1     # q < 1
+    assert L.sfseg_online_push(None, None, 0, None, 0.0, ctypes.byref(nb), 1, 0, 0, None, None) == 1
+    assert L.sfseg_online_destroy(None) == 0
 
 
 def test_binding_refuses_without_library(tmp_path, monkeypatch):
