@@ -35,7 +35,11 @@ constexpr int MT = 128;                 // voxels per MMA tile (rows of A)
 constexpr int RW = MT + 2;              // voxels per loaded row (w halo of 1)
 constexpr int CHUNK_DATA = 3 * RW * 16;    // one 8-channel chunk of 3 frames: 6240 B
 constexpr int CHUNK_BYTES = (CHUNK_DATA + 127) / 128 * 128;   // its stride (128-byte aligned TMA target)
-constexpr int NSLOT = 4;                // input-row ring
+#ifndef SFSEG_NET_NSLOT
+#define SFSEG_NET_NSLOT 4
+#endif
+constexpr int NSLOT = SFSEG_NET_NSLOT;  // input-row ring (rows in flight ahead of the MMAs: NSLOT - 2)
+constexpr int NBAR = 2 * NSLOT + 6;     // full[NSLOT], empty[NSLOT], accf[2], acce[2], wbar, drain
 constexpr int NTHR = 192;               // 6 warps
 constexpr int HR = 32;                  // output rows per CTA
 constexpr long long kSpin = 1ll << 26;
@@ -147,7 +151,7 @@ struct ConvCfg {
     static constexpr int KS = CIN / 16;                       // MMAs per tap
     static constexpr int SLOT_BYTES = NCH * CHUNK_BYTES;
     static constexpr int WBYTES = 27 * KS * 2 * COUT * 16;    // packed weights
-    static constexpr int SMEM = WBYTES + NSLOT * SLOT_BYTES + 16 * 8 + 16 + 128;
+    static constexpr int SMEM = WBYTES + NSLOT * SLOT_BYTES + NBAR * 8 + 16 + 128;
     static constexpr int TMEM_COLS = COUT <= 16 ? 32 : 64;    // two accumulator buffers
 };
 
@@ -160,13 +164,13 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
     unsigned char* wsm = sm;                                   // weights
     unsigned char* ring = sm + C::WBYTES;                      // NSLOT input rows
     uint64_t* bar = reinterpret_cast<uint64_t*>(ring + NSLOT * C::SLOT_BYTES);
-    uint64_t* full = bar;            // [NSLOT]
-    uint64_t* empty = bar + 4;       // [NSLOT]
-    uint64_t* accf = bar + 8;        // [2]
-    uint64_t* acce = bar + 10;       // [2]
-    uint64_t* wbar = bar + 12;
-    uint64_t* drain = bar + 13;      // completion of this CTA's MMAs, awaited after a timeout
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 16);
+    uint64_t* full = bar;                    // [NSLOT]
+    uint64_t* empty = bar + NSLOT;           // [NSLOT]
+    uint64_t* accf = bar + 2 * NSLOT;        // [2]
+    uint64_t* acce = bar + 2 * NSLOT + 2;    // [2]
+    uint64_t* wbar = bar + 2 * NSLOT + 4;
+    uint64_t* drain = bar + 2 * NSLOT + 5;   // completion of this CTA's MMAs, awaited after a timeout
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + NBAR);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // work item: (t, w segment, row range)
@@ -180,7 +184,7 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
     const int nout = he - hs, nin = nout + 2;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 4; ++i) {
+        for (int i = 0; i < NSLOT; ++i) {
             mb_init(&full[i], 1);
             mb_init(&empty[i], 1);
         }
@@ -234,17 +238,20 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
 #pragma unroll 1
                 for (int dh = 0; dh < 3; ++dh) {
                     const uint32_t slot = rbase + (uint32_t)(((j + dh) % NSLOT) * C::SLOT_BYTES);
+                    // Descriptors of this input row and of the taps with this dh; the rest of
+                    // each operand's start address is a compile-time offset added to the
+                    // start-address field (addresses stay below 256 KB and 16-byte aligned, so
+                    // the field, (address mod 2^18) / 16, never carries).
+                    const uint64_t a0 = sdesc(slot, CHUNK_BYTES, 128);
+                    const uint64_t b0 = sdesc(wbase + (uint32_t)(dh * 3 * C::KS * 2 * COUT * 16), COUT * 16, 128);
 #pragma unroll
                     for (int dt = 0; dt < 3; ++dt)
 #pragma unroll
                         for (int dw = 0; dw < 3; ++dw) {
-                            const int tap = (dt * 3 + dh) * 3 + dw;
 #pragma unroll
                             for (int ks = 0; ks < C::KS; ++ks) {
-                                const uint64_t ad = sdesc(slot + (uint32_t)(2 * ks * CHUNK_BYTES + dt * RW * 16 + dw * 16),
-                                                          CHUNK_BYTES, 128);
-                                const uint64_t bd = sdesc(wbase + (uint32_t)((tap * C::KS + ks) * 2 * COUT * 16),
-                                                          COUT * 16, 128);
+                                const uint64_t ad = a0 + (uint64_t)((2 * ks * CHUNK_BYTES + dt * RW * 16 + dw * 16) >> 4);
+                                const uint64_t bd = b0 + (uint64_t)((((dt * 9 + dw) * C::KS + ks) * 2 * COUT * 16) >> 4);
                                 umma(d, ad, bd, id, accum);
                                 accum = 1;
                             }
