@@ -455,3 +455,26 @@ def test_online_start_vectors():
         want = np.zeros((q, H, W))
         want[q - n:] = 1.0 / np.sqrt(n * H * W)
         np.testing.assert_allclose(out[k], want, rtol=1e-14, atol=0)
+
+
+def test_online_diagonal_closed_form():
+    """Radius (0, 0, 0): A = diag(u^2 / alpha), so K steps multiply the start by u^(2K) and the
+    window solutions are closed forms in u.  With q = 2 the second window starts from
+    (x_0, x_0) -- the first window's solution and its copy for the new frame -- and ends at
+    (u_0^(2K) x_0, u_1^(2K) x_0) normalised, x_0 = u_0^(2K) / ||u_0^(2K)||.  Catches a new frame
+    started from the uniform vector instead of the previous newest frame, and a shift in the
+    wrong direction."""
+    rng = np.random.default_rng(24)
+    T, H, W, K, p = 3, 4, 5, 3, 0.4
+    V = rng.uniform(0.2, 1.0, size=(1, T, H, W))
+    out = oracle.online(V, None, 0.0, p, 1.0, (0, 0, 0), q=2, iters=K)
+    u2k = V[0] ** (2 * p * K)
+    x0 = u2k[0] / np.linalg.norm(u2k[0])
+    np.testing.assert_allclose(out[0, 1], x0, rtol=1e-13)
+    np.testing.assert_allclose(out[0, 0], 0.0, atol=0)
+    w1 = np.stack([u2k[0] * x0, u2k[1] * x0])
+    w1 /= np.linalg.norm(w1)
+    np.testing.assert_allclose(out[1], w1, rtol=1e-13)
+    w2 = np.stack([u2k[1] * w1[1], u2k[2] * w1[1]])
+    w2 /= np.linalg.norm(w2)
+    np.testing.assert_allclose(out[2], w2, rtol=1e-13)

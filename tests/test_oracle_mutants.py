@@ -84,3 +84,29 @@ def test_pin_catches_planted_mistake(tmp_path, monkeypatch, name, old, new, targ
     for t in targets:
         with pytest.raises((AssertionError, FloatingPointError)):
             _run_pin(t)
+
+
+# Mistakes planted in the Python-level oracle functions (a modified copy of the function's source
+# is executed in the oracle's namespace and patched in for the duration of the test).
+PY_MUTANTS = [
+    ("online_new_frame_uniform", "online",
+     "newest = xw[-1] if k > 0 else np.ones((H, W))", "newest = np.ones((H, W))",
+     ["test_online_diagonal_closed_form"]),
+    ("online_shift_backwards", "online",
+     "xw = np.concatenate([xw[1:], newest[None]])", "xw = np.concatenate([newest[None], xw[:-1]])",
+     ["test_online_diagonal_closed_form", "test_online_start_vectors"]),
+]
+
+
+@pytest.mark.parametrize("name,func,old,new,targets", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_pin_catches_planted_python_mistake(monkeypatch, name, func, old, new, targets):
+    import inspect
+    import textwrap
+    src = textwrap.dedent(inspect.getsource(getattr(oracle, func)))
+    assert src.count(old) == 1, f"mutation anchor not unique: {old!r}"
+    ns = dict(vars(oracle))
+    exec(compile(src.replace(old, new), f"<mutant {name}>", "exec"), ns)
+    monkeypatch.setattr(oracle, func, ns[func])
+    for t in targets:
+        with pytest.raises((AssertionError, FloatingPointError)):
+            getattr(pins, t)()
