@@ -48,6 +48,15 @@ namespace sfseg {
 int set_last_error(int code, const char* msg) { return fail(code, msg); }
 }  // namespace sfseg
 
+// Layout of the handle's FP64 scratch, in doubles: one disjoint region per use.
+constexpr int kScrRayleigh = 0;      // 4: x'Ax, x'x, the residual sum
+constexpr int kScrApplyAcc = 8;      // 1: norm sum of the adjoint's recomputed iterates
+constexpr int kScrWeightGrad = 16;   // C + 1 <= 65: dL/dw, dL/db
+constexpr int kScrSoftIou = 88;      // 4: soft-IoU sums
+constexpr int kScrMaxKey = 96;       // 1 (an unsigned key): a maximum
+constexpr int kScrSWeights = 104;    // 32 doubles = 64 floats: separate-map unary weights
+constexpr int kScrDoubles = 136;
+
 struct sfseg_handle {
     int C = 0;
     double alpha = 1.0, p = 0.1;
@@ -64,7 +73,7 @@ struct sfseg_handle {
     void* vbuf[2] = {nullptr, nullptr};   // iterate ping-pong, NP floats each
     double* acc = nullptr;            // per-step squared norms
     int acc_cap = 0;
-    double* scratch = nullptr;        // 64 doubles for reductions
+    double* scratch = nullptr;        // kScrDoubles doubles for reductions (layout above)
     unsigned long long* amax = nullptr;
     int* flags = nullptr;
     float* wdev = nullptr;            // channel weights on the device
@@ -220,7 +229,7 @@ int sfseg_create(const sfseg_params* prm, int C, int T, int H, int W, sfseg_hand
     chk(dalloc(&h->f32, (size_t)h->NP));
     chk(dalloc((float**)&h->vbuf[0], (size_t)h->NP));
     chk(dalloc((float**)&h->vbuf[1], (size_t)h->NP));
-    chk(dalloc(&h->scratch, 64));
+    chk(dalloc(&h->scratch, kScrDoubles));
     chk(dalloc(&h->amax, 1));
     chk(dalloc(&h->flags, 1));
     chk(dalloc(&h->wdev, 64));
@@ -307,7 +316,7 @@ int sfseg_set_features_sf(sfseg_handle* h, const void* s_features, int s_dtype, 
         SFSEG_CUDA(cudaMemsetAsync(h->s32, 0, (size_t)h->NP * sizeof(float), s));
     }
     if (int rc = sfseg_set_features(h, f_features, f_dtype, f_weights, f_bias, stream)) return rc;
-    float* swdev = reinterpret_cast<float*>(h->scratch + 32);   // 64 floats of scratch
+    float* swdev = reinterpret_cast<float*>(h->scratch + kScrSWeights);   // 64 floats
     if (Cs > 1) SFSEG_CUDA(cudaMemcpyAsync(swdev, s_weights, sizeof(float) * Cs, cudaMemcpyHostToDevice, s));
     launch_combine(s_features, s_dtype, Cs, h->g, swdev, s_bias, h->s32, nullptr, h->flags, s);
     SFSEG_LAUNCHED();
@@ -470,7 +479,7 @@ int sfseg_rayleigh(sfseg_handle* h, const sfseg_neighborhood* nb, const float* x
     if (!h->features_set) return fail(SFSEG_ERR_STATE, "no features set");
     cudaStream_t s = (cudaStream_t)stream;
     float* y = (float*)h->vbuf[0];
-    double* a = h->scratch;
+    double* a = h->scratch + kScrRayleigh;
     SFSEG_CUDA(cudaMemsetAsync(a, 0, sizeof(double) * 4, s));
     launch_apply_user(x, y, (float*)h->vbuf[1], h->f32, h->g, tp, (float)(1.0 / h->alpha), (float)h->p, h->flags, s,
                       h->sep ? h->s32 : nullptr);
@@ -510,7 +519,7 @@ int sfseg_backward(sfseg_handle* h, const sfseg_neighborhood* nb, const float* g
     if (int rc = ensure_acc(&h->dots, &h->dots_cap, K + 2)) return rc;
     SFSEG_CUDA(cudaMemsetAsync(h->gz, 0, sizeof(float) * h->NP, s));
     SFSEG_CUDA(cudaMemsetAsync(h->dots, 0, sizeof(double) * (K + 1), s));
-    SFSEG_CUDA(cudaMemsetAsync(h->scratch, 0, sizeof(double) * 64, s));
+    SFSEG_CUDA(cudaMemsetAsync(h->scratch, 0, sizeof(double) * kScrDoubles, s));
     float* xK = h->ckpt.back();
     launch_grad_in(grad_x, xK, h->rec_acc + K, h->gbuf[0], h->g, h->dots + K, s);
     SFSEG_LAUNCHED();
@@ -525,7 +534,7 @@ int sfseg_backward(sfseg_handle* h, const sfseg_neighborhood* nb, const float* g
                 xs[i] = xK;
             } else {   // recompute x~_{k0+i} = A x_{k0+i-1} from the recorded norm
                 launch_apply(xs[i - 1], h->g.pitch, h->seg[i], h->g.pitch, h->f32, h->g, tp, inv_alpha, p,
-                             h->rec_acc + k0 + i - 1, h->scratch + 8, h->flags, s);
+                             h->rec_acc + k0 + i - 1, h->scratch + kScrApplyAcc, h->flags, s);
                 SFSEG_LAUNCHED();
                 xs[i] = h->seg[i];
             }
@@ -538,10 +547,11 @@ int sfseg_backward(sfseg_handle* h, const sfseg_neighborhood* nb, const float* g
             gi ^= 1;
         }
     }
-    launch_weight_grad(h->feat_ptr, h->feat_dtype, h->C, h->g, h->gz, h->scratch + 16, s);
+    launch_weight_grad(h->feat_ptr, h->feat_dtype, h->C, h->g, h->gz, h->scratch + kScrWeightGrad, s);
     SFSEG_LAUNCHED();
     std::vector<double> wacc((size_t)h->C + 1);
-    SFSEG_CUDA(cudaMemcpyAsync(wacc.data(), h->scratch + 16, sizeof(double) * (h->C + 1), cudaMemcpyDeviceToHost, s));
+    SFSEG_CUDA(cudaMemcpyAsync(wacc.data(), h->scratch + kScrWeightGrad, sizeof(double) * (h->C + 1),
+                               cudaMemcpyDeviceToHost, s));
     if (int rc = read_flags(h, s)) return rc;
     for (int ch = 0; ch < h->C; ++ch) grad_weights[ch] = (float)wacc[ch];
     *grad_bias = (float)wacc[h->C];
@@ -651,7 +661,7 @@ int sfseg_coarse_start(sfseg_handle* h, const sfseg_neighborhood* nb, int levels
     launch_upsample(h->lvl_x[0], c0->g.T, c0->g.H, c0->g.W, pf[0], pf[1], pf[2], h->g.T, h->g.H, h->g.W, x0_out, s);
     // maximum 1, so that the start vector's scale does not depend on the volume size (it is an
     // input channel of the warm-start network)
-    launch_scale_by_max(x0_out, h->N, reinterpret_cast<unsigned*>(h->scratch + 60), s);
+    launch_scale_by_max(x0_out, h->N, reinterpret_cast<unsigned*>(h->scratch + kScrMaxKey), s);
     SFSEG_LAUNCHED();
     return SFSEG_OK;
 }
@@ -670,7 +680,7 @@ int sfseg_soft_binarize(sfseg_handle* h, const sfseg_neighborhood* nb, int iters
     const float inv_alpha = (float)(1.0 / h->alpha), p = (float)h->p;
     float* y = (float*)h->vbuf[0];                     // A x, caller layout
     float* v = (float*)h->vbuf[1];                     // u * x, internal layout
-    unsigned* key = reinterpret_cast<unsigned*>(h->scratch + 60);
+    unsigned* key = reinterpret_cast<unsigned*>(h->scratch + kScrMaxKey);
     const bool fast = fast_iterate_supported(tp);
     const float* s32 = h->sep ? h->s32 : nullptr;
     for (int k = 0; k < iters; ++k) {
@@ -702,7 +712,7 @@ int sfseg_soft_iou_loss(sfseg_handle* h, const float* x, const float* target, do
     if (int rc = check_handle(h)) return rc;
     if (!x || !target || !loss) return fail(SFSEG_ERR_INVALID_ARG, "null argument");
     cudaStream_t s = (cudaStream_t)stream;
-    double* a = h->scratch + 48;
+    double* a = h->scratch + kScrSoftIou;
     SFSEG_CUDA(cudaMemsetAsync(a, 0, sizeof(double) * 4, s));
     SFSEG_CUDA(cudaMemsetAsync(h->amax, 0, sizeof(unsigned long long), s));
     launch_soft_iou(x, target, h->N, grad_x, a, h->amax, s);

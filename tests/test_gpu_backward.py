@@ -147,3 +147,20 @@ def test_autograd_function():
         gw, gb = h.backward(g, (1, 3, 3))
     np.testing.assert_allclose(w.grad.numpy(), gw, rtol=1e-3, atol=1e-6)
     assert abs(b.grad.item() - gb) <= 1e-3 * max(1.0, abs(gb))
+
+
+def test_adjoint_with_the_maximum_channel_count():
+    """C = 64 (the largest the handle takes): every weight's gradient against the oracle's
+    reverse pass (each channel's gradient lands in its own slot of the handle's scratch)."""
+    rng = np.random.default_rng(13)
+    C, T, H, W = 64, 2, 8, 9
+    V = rng.uniform(0.0, 1.0, size=(C, T, H, W)).astype(np.float32)
+    w = (rng.normal(size=C) * 0.3).astype(np.float32)
+    c = rng.normal(size=(T, H, W)).astype(np.float32)
+    r = (1, 1, 2)
+    _, gw, gb = _gpu_grad(V, w, -0.2, r, 4, 2, lambda h, x: torch.from_numpy(c).cuda())
+    gwo, gbo = oracle.grad_csr(V.astype(np.float64), w.astype(np.float64), -0.2, 0.1, 1.0, r,
+                               np.ones(V[0].size), 4, c.astype(np.float64))
+    scale = max(np.abs(gwo).max(), abs(gbo))
+    assert np.abs(gw - gwo).max() <= 2e-4 * scale
+    assert abs(gb - gbo) <= 2e-4 * scale
