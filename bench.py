@@ -306,6 +306,46 @@ def bench_r133_storage(sfseg, synth, steps: int = 10):
     return out
 
 
+def bench_adjoint(sfseg, synth, steps: int = 5):
+    """The learning workload (Sec. 3.4): C = 8 float32 channels of 32 x 240 x 427, radius (1,3,3),
+    30 unrolled iterations recorded with a checkpoint every 5, loss 1 - soft-IoU against the
+    noiseless mask, and the hand-written adjoint back to the 8 channel weights and the bias.
+    CUDA-event times of the recorded forward, the loss and the backward, per step."""
+    import torch
+    Tb, Hb, Wb, K = 32, 240, 427, 30
+    V, m, w = synth.multichannel(Tb, Hb, Wb, C=8, seed=4003)
+    feats = torch.from_numpy(V).cuda()
+    tgt = torch.from_numpy((m > 0.5).astype("float32")).cuda()
+    w = (w * 8.0).astype("float32")
+    h = sfseg.PowerIteration(8, Tb, Hb, Wb)
+    x = torch.empty((Tb, Hb, Wb), device="cuda")
+
+    def run():
+        h.power_iterate(feats, w, -2.0, (1, 3, 3), iters=K, x=x, record_every=5)
+        e1.record()
+        _, g = h.soft_iou_loss(x, tgt)
+        h.backward(g, (1, 3, 3))
+
+    e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+    for _ in range(2):
+        run()
+    torch.cuda.synchronize()
+    t_fwd = t_bwd = 0.0
+    for _ in range(steps):
+        e0.record()
+        run()
+        e2.record()
+        torch.cuda.synchronize()
+        t_fwd += e0.elapsed_time(e1)
+        t_bwd += e1.elapsed_time(e2)
+    h.close()
+    nvox = Tb * Hb * Wb
+    return {"workload": "C=8 fp32 32x240x427, radius (1,3,3), 30 iterations, checkpoint every 5, 1 - soft-IoU",
+            "forward_ms": t_fwd / steps, "loss_and_backward_ms": t_bwd / steps,
+            "backward_over_forward": t_bwd / max(t_fwd, 1e-9),
+            "forward_voxel_iterations_per_s": nvox * K / (t_fwd / steps * 1e-3)}
+
+
 def bench_separate_maps(sfseg, synth, steps: int = 5):
     """Separate unary and pairwise maps (Eq. 9 with two channel sets) at the 480p shape: S_m from
     the crossing-blobs volume, F_m from a second draw of it, radius (2,7,7), 50 iterations,
@@ -509,6 +549,7 @@ def main():
             out["soft_binarize"] = bench_soft_binarize(sfseg, synth)
             out["online"] = bench_online(sfseg, synth)
             out["separate_maps"] = bench_separate_maps(sfseg, synth)
+            out["adjoint"] = bench_adjoint(sfseg, synth)
             out["r133_storage"] = bench_r133_storage(sfseg, synth)
             out["time_to_residual"] = bench_time_to_residual(sfseg, synth, warmstart)
         if world == 1 and not args.no_cpu_baseline:
