@@ -86,6 +86,7 @@ struct sfseg_handle {
     // adjoint workspace
     float* gbuf[2] = {nullptr, nullptr};
     float* gz = nullptr;
+    float* adjw[4] = {nullptr, nullptr, nullptr, nullptr};   // TMA-path adjoint workspace
     std::vector<float*> seg;
     double* dots = nullptr;
     int dots_cap = 0;
@@ -254,6 +255,7 @@ int sfseg_destroy(sfseg_handle* h) {
     cudaFree(h->vbuf[1]);
     cudaFree(h->acc);
     cudaFree(h->scratch);
+    for (float* q : h->adjw) cudaFree(q);
     cudaFree(h->amax);
     cudaFree(h->flags);
     cudaFree(h->wdev);
@@ -511,6 +513,10 @@ int sfseg_backward(sfseg_handle* h, const sfseg_neighborhood* nb, const float* g
     for (int i = 0; i < 2; ++i)
         if (!h->gbuf[i]) SFSEG_CUDA(dalloc(&h->gbuf[i], (size_t)h->NP));
     if (!h->gz) SFSEG_CUDA(dalloc(&h->gz, (size_t)h->NP));
+    const bool fast_adj = fast_iterate_supported(tp);
+    if (fast_adj)
+        for (float*& q : h->adjw)
+            if (!q) SFSEG_CUDA(dalloc(&q, (size_t)h->NP));
     while ((int)h->seg.size() < c + 1) {
         float* q = nullptr;
         SFSEG_CUDA(dalloc(&q, (size_t)h->NP));
@@ -533,16 +539,21 @@ int sfseg_backward(sfseg_handle* h, const sfseg_neighborhood* nb, const float* g
             if (k0 + i == K) {
                 xs[i] = xK;
             } else {   // recompute x~_{k0+i} = A x_{k0+i-1} from the recorded norm
-                launch_apply(xs[i - 1], h->g.pitch, h->seg[i], h->g.pitch, h->f32, h->g, tp, inv_alpha, p,
-                             h->rec_acc + k0 + i - 1, h->scratch + kScrApplyAcc, h->flags, s);
+                if (!(fast_adj && launch_apply_internal_fast(xs[i - 1], h->seg[i], h->adjw[0], h->f32, h->g, tp,
+                                                             inv_alpha, p, h->rec_acc + k0 + i - 1, h->flags, s)))
+                    launch_apply(xs[i - 1], h->g.pitch, h->seg[i], h->g.pitch, h->f32, h->g, tp, inv_alpha, p,
+                                 h->rec_acc + k0 + i - 1, h->scratch + kScrApplyAcc, h->flags, s);
                 SFSEG_LAUNCHED();
                 xs[i] = h->seg[i];
             }
         }
         for (int k = k1 - 1; k >= k0; --k) {
             float* gnext = k > 0 ? h->gbuf[gi ^ 1] : nullptr;
-            launch_adjoint_step(xs[k - k0], h->rec_acc + k, xs[k + 1 - k0], h->rec_acc + k + 1, h->gbuf[gi],
-                                h->dots + k + 1, gnext, h->dots + k, h->gz, h->f32, h->g, tp, inv_alpha, p, s);
+            if (!(fast_adj && launch_adjoint_step_fast(xs[k - k0], h->rec_acc + k, xs[k + 1 - k0], h->rec_acc + k + 1,
+                                                       h->gbuf[gi], h->dots + k + 1, gnext, h->dots + k, h->gz,
+                                                       h->f32, h->g, tp, inv_alpha, p, h->adjw, h->flags, s)))
+                launch_adjoint_step(xs[k - k0], h->rec_acc + k, xs[k + 1 - k0], h->rec_acc + k + 1, h->gbuf[gi],
+                                    h->dots + k + 1, gnext, h->dots + k, h->gz, h->f32, h->g, tp, inv_alpha, p, s);
             SFSEG_LAUNCHED();
             gi ^= 1;
         }

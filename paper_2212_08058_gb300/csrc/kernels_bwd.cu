@@ -19,6 +19,7 @@
 #include "common.cuh"
 #include "launch.h"
 #include "stencil.cuh"
+#include "voxels.cuh"
 
 namespace sfseg {
 
@@ -96,6 +97,74 @@ void launch_adjoint_step(const float* xk, const double* acc_k, const float* xn, 
     op.p = p;
     op.sk = op.sn = op.dotn = 0.f;
     run_stencil(op, tp, 8, nullptr, dot_k, nullptr, nullptr, s);
+}
+
+// ---- the same step on the TMA kernel: two filtering passes instead of one six-signal pass.
+// With Q = a1 c0 - p c1 + a3 c2 (kernels_fast.cu, MODE 1/2) for the signals of u x (Q_x) and of
+// u g_y (Q_g), the feature term above is (1 - f) u (g_y Q_x + x Q_g), and g_k = A g_y.
+
+// v_x = u x_k, v_g = u g_y (internal layout).
+__global__ void adjoint_prep_kernel(const float* xk, const double* acc_k, const float* xn, const double* acc_n,
+                                    const float* gn, const double* dot_n, const float* f, float p, Geom g, float* vx,
+                                    float* vg, int* flags) {
+    const float sk = inv_norm_from(acc_k, flags), sn = inv_norm_from(acc_n, flags);
+    const float dotn = (float)*dot_n;
+    for_each_voxel(g, [&](int64_t, int64_t j) {
+        const float u = unary_pow(f[j], p);
+        vx[j] = u * (sk * xk[j]);
+        vg[j] = u * ((gn[j] - sn * xn[j] * dotn) * sn);
+    });
+}
+
+// gz += (1 - f) u (g_y Q_x + x Q_g), dot_k += <x_k, g_k>.
+__global__ void adjoint_combine_kernel(const float* xk, const double* acc_k, const float* xn, const double* acc_n,
+                                       const float* gn, const double* dot_n, const float* f, float p, Geom g,
+                                       const float* qx, const float* qg, const float* gk, float* gz, double* dot_k) {
+    const float sk = inv_norm_from(acc_k, nullptr), sn = inv_norm_from(acc_n, nullptr);
+    const float dotn = (float)*dot_n;
+    float part = 0.f;
+    for_each_voxel(g, [&](int64_t, int64_t j) {
+        const float fv = f[j];
+        const float u = unary_pow(fv, p);
+        const float x = sk * xk[j];
+        const float gy = (gn[j] - sn * xn[j] * dotn) * sn;
+        part += x * gk[j];
+        gz[j] += (1.f - fv) * u * (gy * qx[j] + x * qg[j]);
+    });
+    const double b = block_sum((double)part);
+    if (threadIdx.x == 0) atomicAdd(dot_k, b);
+}
+
+bool launch_adjoint_step_fast(const float* xk, const double* acc_k, const float* xn, const double* acc_n,
+                              const float* gn, const double* dot_n, float* gk_out, double* dot_k, float* gz,
+                              const float* f32, Geom g, const Taps& tp, float inv_alpha, float p, float* const work[4],
+                              int* flags, cudaStream_t s) {
+    if (!fast_iterate_supported(tp)) return false;
+    const RowLaunch rl = row_launch(g, num_sms(), 8);
+    adjoint_prep_kernel<<<rl.blocks, rl.threads, 0, s>>>(xk, acc_k, xn, acc_n, gn, dot_n, f32, p, g, work[0], work[1],
+                                                         flags);
+    count_launches(1);
+    if (!launch_filter_fast(work[0], 1, work[2], nullptr, f32, g, tp, inv_alpha, p, nullptr, flags, s)) return false;
+    float* gk = gk_out ? gk_out : work[0];   // v_x is consumed by now
+    if (!launch_filter_fast(work[1], 2, gk, work[3], f32, g, tp, inv_alpha, p, nullptr, flags, s)) return false;
+    adjoint_combine_kernel<<<rl.blocks, rl.threads, 0, s>>>(xk, acc_k, xn, acc_n, gn, dot_n, f32, p, g, work[2],
+                                                            work[3], gk, gz, dot_k);
+    count_launches(1);
+    return true;
+}
+
+// v = u x, both in the internal layout.
+__global__ void state_internal_kernel(const float* x, const float* f, float p, Geom g, float* v) {
+    for_each_voxel(g, [&](int64_t, int64_t j) { v[j] = unary_pow(f[j], p) * x[j]; });
+}
+
+bool launch_apply_internal_fast(const float* x, float* y, float* v, const float* f32, Geom g, const Taps& tp,
+                                float inv_alpha, float p, const double* acc_in, int* flags, cudaStream_t s) {
+    if (!fast_iterate_supported(tp)) return false;
+    const RowLaunch rl = row_launch(g, num_sms());
+    state_internal_kernel<<<rl.blocks, rl.threads, 0, s>>>(x, f32, p, g, v);
+    count_launches(1);
+    return launch_filter_fast(v, 3, y, nullptr, f32, g, tp, inv_alpha, p, acc_in, flags, s);
 }
 
 // g_K from the caller's layout into the internal layout, and <x_K, g_K>.

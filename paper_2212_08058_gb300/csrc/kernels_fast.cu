@@ -136,11 +136,18 @@ struct Params {
     void* out;        // next state (internal pitch) or x~ (caller layout)
     const void* f;    // f in global memory (internal pitch), read by the epilogue
     const float* s;   // separate unary map S_m (float32, internal pitch; SEP kernels only)
+    void* out2;       // second output of the adjoint filtering (MODE 2)
 };
 
 // SEP: the unary term u = s^p comes from a separate map S_m (Eq. 9 with its own channels)
-// instead of from f.
-template <int RT, int RH, int RW, typename TS, typename TVO, bool OUT_X, bool SEP>
+// instead of from f.  MODE 0 is the power-iteration step.  MODEs 1 and 2 serve the adjoint
+// (kernels_bwd.cu): with c_0, c_1, c_2 the three filtered signals of the input (G*(u z),
+// G*(f^2 u z), G*(f u z) for v = u z), MODE 1 stores Q = a1 c_0 - p c_1 + a3 c_2 with
+// a1 = p (1/alpha - f^2) - 2 f^2, a3 = 2 (p + 1) f (the f-derivative weights of the step), and
+// MODE 2 stores A z = u B (B the Eq. 7 bracket) and Q, MODE 3 only A z; all scaled by s, in the
+// internal layout.  MODE 4 is the power-iteration step that also records x~ (internal layout,
+// out2) for the adjoint.
+template <int RT, int RH, int RW, typename TS, typename TVO, bool OUT_X, bool SEP, int MODE>
 __global__ void __launch_bounds__(NTHR, SFSEG_FAST_MINB)
 iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtensorMap mf, Params P) {
     using C = Cfg<RT, RH, RW, TS, TVO, OUT_X>;
@@ -325,18 +332,67 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
         // ---------------- Eq. 7 combination for frame to = tt - RT
         if (to >= t0 && wr < TH) {
             float2 outv[4];
+            float2 outq[(MODE == 2 || MODE == 4) ? 4 : 1];
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 const float2 fv = fo[m];
                 const float2 sv = SEP ? so[SEP ? m : 0] : fv;
                 const float2 u = make_float2(unary_pow_fast(sv.x, P.p), unary_pow_fast(sv.y, P.p));
                 const float2 e = fma2(make_float2(-fv.x, -fv.y), fv, f2(P.inv_alpha));   // 1/alpha - f^2
-                float2 B = fma2(e, y[0][m], make_float2(-y[1][m].x, -y[1][m].y));
-                B = fma2(mul2(f2(2.f), fv), y[2][m], B);
-                const float2 xt = mul2(mul2(s2, u), B);
-                part = fma2(xt, xt, part);
-                outv[m] = OUT_X ? xt : mul2(u, xt);
+                if constexpr (MODE == 0 || MODE == 4) {
+                    float2 B = fma2(e, y[0][m], make_float2(-y[1][m].x, -y[1][m].y));
+                    B = fma2(mul2(f2(2.f), fv), y[2][m], B);
+                    const float2 xt = mul2(mul2(s2, u), B);
+                    part = fma2(xt, xt, part);
+                    outv[m] = OUT_X ? xt : mul2(u, xt);
+                    if constexpr (MODE == 4) outq[m] = xt;
+                } else if constexpr (MODE == 3) {
+                    float2 B = fma2(e, y[0][m], make_float2(-y[1][m].x, -y[1][m].y));
+                    B = fma2(mul2(f2(2.f), fv), y[2][m], B);
+                    outv[m] = mul2(mul2(s2, u), B);
+                } else {
+                    const float2 a1 = fma2(f2(P.p), e, mul2(f2(-2.f), mul2(fv, fv)));
+                    const float2 a3 = mul2(f2(2.f * (P.p + 1.f)), fv);
+                    float2 Q = fma2(a1, y[0][m], mul2(f2(-P.p), y[1][m]));
+                    Q = mul2(s2, fma2(a3, y[2][m], Q));
+                    if constexpr (MODE == 1) {
+                        outv[m] = Q;
+                    } else {
+                        float2 B = fma2(e, y[0][m], make_float2(-y[1][m].x, -y[1][m].y));
+                        B = fma2(mul2(f2(2.f), fv), y[2][m], B);
+                        outv[m] = mul2(mul2(s2, u), B);
+                        outq[MODE == 2 ? m : 0] = Q;
+                    }
+                }
             }
+            if constexpr (MODE == 4) {
+                if (h < g.H) {
+                    float* o2 = reinterpret_cast<float*>(P.out2) + ((int64_t)to * g.H + h) * g.pitch + wbase;
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        if (wbase + 2 * m < g.W) o2[2 * m] = outq[m].x;
+                        if (wbase + 2 * m + 1 < g.W) o2[2 * m + 1] = outq[m].y;
+                    }
+                }
+            }
+            if constexpr (MODE != 0 && MODE != 4) {
+                if (h < g.H) {
+                    float* o = reinterpret_cast<float*>(P.out) + ((int64_t)to * g.H + h) * g.pitch + wbase;
+                    float* o2 = MODE == 2 ? reinterpret_cast<float*>(P.out2) + ((int64_t)to * g.H + h) * g.pitch + wbase
+                                          : nullptr;
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        if (wbase + 2 * m < g.W) {
+                            o[2 * m] = outv[m].x;
+                            if (MODE == 2) o2[2 * m] = outq[MODE == 2 ? m : 0].x;
+                        }
+                        if (wbase + 2 * m + 1 < g.W) {
+                            o[2 * m + 1] = outv[m].y;
+                            if (MODE == 2) o2[2 * m + 1] = outq[MODE == 2 ? m : 0].y;
+                        }
+                    }
+                }
+            } else
             if (h < g.H) {
                 if (OUT_X) {
                     float* o = reinterpret_cast<float*>(P.out) + ((int64_t)to * g.H + h) * g.W + wbase;
@@ -435,15 +491,15 @@ static int pick_chunk(int T, int tiles, int slots, int rt) {
     return best;
 }
 
-template <int RT, int RH, int RW, typename TS, typename TVO, bool OUT_X, bool SEP = false>
+template <int RT, int RH, int RW, typename TS, typename TVO, bool OUT_X, bool SEP = false, int MODE = 0>
 static bool launch_t(const void* vin, void* out, const void* f, const Geom& g, const Taps& tp, float inv_alpha,
                      float p, const double* acc_in, double* acc_out, int* flags, cudaStream_t s,
-                     const float* s32 = nullptr) {
+                     const float* s32 = nullptr, void* out2 = nullptr) {
     using C = Cfg<RT, RH, RW, TS, TVO, OUT_X>;
     constexpr bool bf = sizeof(TS) == 2;
     CUtensorMap mv, mf;
     if (!make_map(&mv, vin, bf, g, C::BH) || !make_map(&mf, f, bf, g, C::BH)) return false;
-    auto kern = iter_fast<RT, RH, RW, TS, TVO, OUT_X, SEP>;
+    auto kern = iter_fast<RT, RH, RW, TS, TVO, OUT_X, SEP, MODE>;
     static int slots_per_sm = -1;
     if (slots_per_sm < 0) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess) return false;
@@ -460,6 +516,7 @@ static bool launch_t(const void* vin, void* out, const void* f, const Geom& g, c
     for (int i = 0; i < 2 * kMaxRW + 1; ++i) P.gw[i] = make_float2(tp.gw[i], tp.gw[i]);
     P.f = f;
     P.s = s32;
+    P.out2 = out2;
     const int tx = (g.W + TW - 1) / TW, ty = (g.H + TH - 1) / TH;
     P.tchunk = pick_chunk(g.T, tx * ty, slots_per_sm * num_sms(), RT);
     P.acc_in = acc_in;
@@ -491,6 +548,29 @@ static bool dispatch(const void* vin, int vin_type, void* out, int out_type, boo
     return launch_t<RT, RH, RW, bf, float, false>(vin, out, f, g, tp, ia, p, ai, ao, fl, s);
 }
 
+// The recording step (MODE 4), float32 only.
+template <int RT, int RH, int RW>
+static bool dispatch_ckpt(const float* vin, void* out, bool out_x, const float* f, const Geom& g, const Taps& tp,
+                          float ia, float p, const double* ai, double* ao, float* ckpt, int* fl, cudaStream_t s) {
+    if (out_x)
+        return launch_t<RT, RH, RW, float, float, true, false, 4>(vin, out, f, g, tp, ia, p, ai, ao, fl, s, nullptr,
+                                                                ckpt);
+    return launch_t<RT, RH, RW, float, float, false, false, 4>(vin, out, f, g, tp, ia, p, ai, ao, fl, s, nullptr,
+                                                             ckpt);
+}
+
+// The adjoint's filtering passes (MODE 1: Q; MODE 2: A z and Q; MODE 3: A z), float32 only.
+template <int RT, int RH, int RW>
+static bool dispatch_filter(const float* vin, int mode, float* out, float* out2, const float* f, const Geom& g,
+                            const Taps& tp, float ia, float p, const double* ai, int* fl, cudaStream_t s) {
+    if (mode == 1)
+        return launch_t<RT, RH, RW, float, float, false, false, 1>(vin, out, f, g, tp, ia, p, ai, nullptr, fl, s);
+    if (mode == 3)
+        return launch_t<RT, RH, RW, float, float, false, false, 3>(vin, out, f, g, tp, ia, p, ai, nullptr, fl, s);
+    return launch_t<RT, RH, RW, float, float, false, false, 2>(vin, out, f, g, tp, ia, p, ai, nullptr, fl, s, nullptr,
+                                                             out2);
+}
+
 }  // namespace fast
 
 // Radii with a compiled kernel: the method's (1,3,3) and (2,7,7), and (1,4,4), (1,2,2), the
@@ -511,6 +591,28 @@ bool launch_iterate_fast(const void* vin, int vin_type, void* out, int out_type,
     if (tp.rt == A && tp.rh == B && tp.rw == C)                                                             \
         return fast::dispatch<A, B, C>(vin, vin_type, out, out_type, out_x, f, g, tp, inv_alpha, p, acc_in, \
                                        acc_out, flags, s, s32);
+    SFSEG_FAST_RADII(SFSEG_GO)
+#undef SFSEG_GO
+    return false;
+}
+
+bool launch_iterate_fast_ckpt(const float* vin, void* out, bool out_x, const float* f, const Geom& g, const Taps& tp,
+                              float inv_alpha, float p, const double* acc_in, double* acc_out, float* ckpt, int* flags,
+                              cudaStream_t s) {
+#define SFSEG_GO(A, B, C)                                                                                        \
+    if (tp.rt == A && tp.rh == B && tp.rw == C)                                                                  \
+        return fast::dispatch_ckpt<A, B, C>(vin, out, out_x, f, g, tp, inv_alpha, p, acc_in, acc_out, ckpt, flags, \
+                                            s);
+    SFSEG_FAST_RADII(SFSEG_GO)
+#undef SFSEG_GO
+    return false;
+}
+
+bool launch_filter_fast(const float* vin, int mode, float* out, float* out2, const float* f, const Geom& g,
+                        const Taps& tp, float inv_alpha, float p, const double* acc_in, int* flags, cudaStream_t s) {
+#define SFSEG_GO(A, B, C)                                                                                     \
+    if (tp.rt == A && tp.rh == B && tp.rw == C)                                                               \
+        return fast::dispatch_filter<A, B, C>(vin, mode, out, out2, f, g, tp, inv_alpha, p, acc_in, flags, s);
     SFSEG_FAST_RADII(SFSEG_GO)
 #undef SFSEG_GO
     return false;

@@ -136,10 +136,14 @@ void launch_iterate(const void* vin, int vin_type, void* out, int out_type, bool
                     int f_type, float* ckpt, Geom g, const Taps& tp, float inv_alpha, float p,
                     const double* acc_in, double* acc_out, int* flags, cudaStream_t s, const float* s32) {
     using bf = __nv_bfloat16;
-    // The TMA kernel serves the method's radii; recording checkpoints uses the generic one.
+    // The TMA kernel serves the method's radii, recording steps (float32, shared maps) included.
     if (ckpt == nullptr && fast_iterate_supported(tp) &&
         launch_iterate_fast(vin, vin_type, out, out_type, out_x, f, g, tp, inv_alpha, p, acc_in, acc_out, flags, s,
                             s32))
+        return;
+    if (ckpt != nullptr && vin_type == kF32 && s32 == nullptr && fast_iterate_supported(tp) &&
+        launch_iterate_fast_ckpt((const float*)vin, out, out_x, (const float*)f, g, tp, inv_alpha, p, acc_in, acc_out,
+                                 ckpt, flags, s))
         return;
 #define SFSEG_IT(TVI, TVO, TF, OX) \
     iterate_t<TVI, TVO, TF, OX>(vin, out, f, ckpt, g, tp, inv_alpha, p, acc_in, acc_out, flags, s, s32)

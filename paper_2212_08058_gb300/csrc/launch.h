@@ -43,6 +43,19 @@ bool launch_iterate_fast(const void* vin, int vin_type, void* out, int out_type,
                          const Geom& g, const Taps& tp, float inv_alpha, float p, const double* acc_in,
                          double* acc_out, int* flags, cudaStream_t s, const float* s32 = nullptr);
 
+// The TMA step that also records x~_{k+1} (internal layout) into ckpt, float32 storage; false
+// (nothing launched) for a radius without a compiled kernel.
+bool launch_iterate_fast_ckpt(const float* vin, void* out, bool out_x, const float* f, const Geom& g, const Taps& tp,
+                              float inv_alpha, float p, const double* acc_in, double* acc_out, float* ckpt, int* flags,
+                              cudaStream_t s);
+
+// The adjoint's filtering passes on the TMA kernel (kernels_fast.cu), float32, internal layout:
+// for v = u z (scaled by s = 1/sqrt(*acc_in), or 1), mode 1 writes Q = s (a1 c0 - p c1 + a3 c2)
+// to out; mode 2 writes A z (scaled) to out and Q to out2; mode 3 writes only A z.  Returns
+// false (nothing launched) for a radius without a compiled kernel.
+bool launch_filter_fast(const float* vin, int mode, float* out, float* out2, const float* f, const Geom& g,
+                        const Taps& tp, float inv_alpha, float p, const double* acc_in, int* flags, cudaStream_t s);
+
 // y = s * A x in the plain (x-space) form: x with pitch x_pitch, y with pitch y_pitch, FP32
 // features; s = 1/sqrt(*acc_in) (or 1 if acc_in is null); acc_out += ||y||^2 (nullable).
 void launch_apply(const float* x, int x_pitch, float* y, int y_pitch, const float* f32, Geom g,
@@ -97,6 +110,17 @@ void launch_adjoint_step(const float* xk, const double* acc_k, const float* xn, 
                          const float* gn, const double* dot_n, float* gk_out, double* dot_k,
                          float* gz, const float* f32, Geom g, const Taps& tp, float inv_alpha,
                          float p, cudaStream_t s);
+// The same step through the TMA kernel's filtering passes (false, with nothing or only the
+// preparation launched, for a radius without a TMA kernel: then run launch_adjoint_step).
+// work: four internal-layout float volumes.
+bool launch_adjoint_step_fast(const float* xk, const double* acc_k, const float* xn, const double* acc_n,
+                              const float* gn, const double* dot_n, float* gk_out, double* dot_k, float* gz,
+                              const float* f32, Geom g, const Taps& tp, float inv_alpha, float p, float* const work[4],
+                              int* flags, cudaStream_t s);
+// y = s A x for x, y in the internal layout (s = 1/sqrt(*acc_in)) through the TMA kernel, v a
+// scratch volume; false (only the conversion launched) for a radius without a TMA kernel.
+bool launch_apply_internal_fast(const float* x, float* y, float* v, const float* f32, Geom g, const Taps& tp,
+                                float inv_alpha, float p, const double* acc_in, int* flags, cudaStream_t s);
 void launch_weight_grad(const void* feat, int feat_dtype, int C, Geom g, const float* gz,
                         double* acc_c_plus_1, cudaStream_t s);
 void launch_soft_iou(const float* x, const float* tgt, int64_t n, float* grad, double* acc,

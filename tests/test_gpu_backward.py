@@ -35,16 +35,18 @@ def _gpu_grad(V, w, b, radius, K, every, grad_fn, p=0.1, alpha=1.0):
         return x.cpu().numpy().astype(np.float64), gw.astype(np.float64), gb
 
 
-@pytest.mark.parametrize("K,every", [(6, 2), (6, 4), (5, 5), (1, 3)])
-def test_adjoint_matches_oracle_gradient(K, every):
+@pytest.mark.parametrize("K,every,r", [(6, 2, (1, 2, 2)), (6, 4, (1, 2, 2)), (5, 5, (1, 2, 2)), (1, 3, (1, 2, 2)),
+                                        (6, 2, (1, 3, 3)), (5, 5, (2, 7, 7)), (3, 2, (1, 1, 2))])
+def test_adjoint_matches_oracle_gradient(K, every, r):
     """Linear loss <c, x_K>: the GPU adjoint equals the oracle's reverse pass on the explicit
-    Eq. 2 matrix (4 x 12 x 12, C = 2), for several checkpoint spacings."""
+    Eq. 2 matrix (4 x 12 x 12, C = 2), for several checkpoint spacings; radii with a TMA kernel
+    ((1,2,2), (1,3,3), (2,7,7): the two-pass adjoint step) and without ((1,1,2): the six-signal
+    stencil)."""
     V, _, _ = synth.multichannel(4, 12, 12, C=2, seed=4001)
     w = np.array([1.4, -0.7], dtype=np.float32)
     b = 0.1
     rng = np.random.default_rng(11)
     c = rng.normal(size=V.shape[1:]).astype(np.float32)
-    r = (1, 2, 2)
     _, gw, gb = _gpu_grad(V, w, b, r, K, every, lambda h, x: torch.from_numpy(c).cuda())
     gwo, gbo = oracle.grad_csr(V.astype(np.float64), w.astype(np.float64), b, 0.1, 1.0, r,
                                np.ones(V[0].size), K, c.astype(np.float64))
