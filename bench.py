@@ -306,6 +306,32 @@ def bench_r133_storage(sfseg, synth, steps: int = 10):
     return out
 
 
+def bench_small_graphs(sfseg, synth, calls: int = 100):
+    """The small drifting-blob case (C = 1, 8 x 64 x 64, radius (1,3,3), 20 iterations), where
+    launch latency dominates: CUDA-event time per power_iterate call with direct launches and
+    with the call replayed from a captured CUDA graph (sfseg_enable_graphs)."""
+    import torch
+    V = torch.from_numpy(synth.drifting_blob(8, 64, 64, seed=1000)).cuda()
+    out = {"workload": "drifting blob C=1 8x64x64, radius (1,3,3), 20 iterations per call"}
+    for name, on in (("direct_ms_per_call", False), ("graph_ms_per_call", True)):
+        h = sfseg.PowerIteration(1, 8, 64, 64)
+        h.set_features(V)
+        h.enable_graphs(on)
+        x = torch.empty((8, 64, 64), device="cuda")
+        for _ in range(5):
+            h.power_iterate(None, radius=(1, 3, 3), iters=20, x=x)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(calls):
+            h.power_iterate(None, radius=(1, 3, 3), iters=20, x=x)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = e0.elapsed_time(e1) / calls
+        h.close()
+    return out
+
+
 def bench_adjoint(sfseg, synth, steps: int = 5):
     """The learning workload (Sec. 3.4): C = 8 float32 channels of 32 x 240 x 427, radius (1,3,3),
     30 unrolled iterations recorded with a checkpoint every 5, loss 1 - soft-IoU against the
@@ -550,6 +576,7 @@ def main():
             out["online"] = bench_online(sfseg, synth)
             out["separate_maps"] = bench_separate_maps(sfseg, synth)
             out["adjoint"] = bench_adjoint(sfseg, synth)
+            out["small_graphs"] = bench_small_graphs(sfseg, synth)
             out["r133_storage"] = bench_r133_storage(sfseg, synth)
             out["time_to_residual"] = bench_time_to_residual(sfseg, synth, warmstart)
         if world == 1 and not args.no_cpu_baseline:

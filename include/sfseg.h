@@ -194,7 +194,8 @@ int sfseg_soft_binarize(sfseg_handle* h, const sfseg_neighborhood* nb, int iters
 typedef struct sfseg_online sfseg_online;
 
 /* A stream of C-channel frames of H x W with a sub-window of q >= 1 frames.  Allocates a handle
- * of q frames plus two window solutions (about 7 q H W floats). */
+ * of q frames plus two window solutions (about 7 q H W floats); the window's iterations run as
+ * replayed CUDA graphs (sfseg_enable_graphs). */
 int sfseg_online_create(const sfseg_params* params, int C, int q, int H, int W, sfseg_online** out);
 int sfseg_online_destroy(sfseg_online* stream_handle);
 
@@ -275,6 +276,16 @@ int sfseg_warmstart(sfseg_handle* h, sfseg_net* net, const void* features, int d
  * completes.  Returns SFSEG_ERR_TIMEOUT -- the expected outcome -- and leaves the handle and the
  * CUDA context usable.  Synchronises. */
 int sfseg_selftest_wait(sfseg_handle* h, long long spins, void* stream);
+
+/* CUDA graphs for launch-bound calls (no counterpart in the paper).  When enabled, a call of
+ * sfseg_power_iterate that passes features == NULL (features already set), records nothing,
+ * asks for no norms and is not being timed runs its launch sequence as a CUDA graph: the first
+ * call for given pointers and parameters (x_inout, iters, iters_bf16, init, neighbourhood, the
+ * handle's buffers) captures it, later ones replay it.  The graph runs on a stream of the handle,
+ * ordered after the work already queued on the caller's stream and before the work queued
+ * after the call; results are identical.  Worth it for small volumes, where launch latency
+ * dominates.  Off by default. */
+int sfseg_enable_graphs(sfseg_handle* h, int on);
 
 /* Instrumentation (no counterpart in the paper).  When enabled, each sfseg_power_iterate call
  * records two CUDA events on its stream, before its first and after its last iteration-kernel

@@ -57,6 +57,25 @@ constexpr int kScrMaxKey = 96;       // 1 (an unsigned key): a maximum
 constexpr int kScrSWeights = 104;    // 32 doubles = 64 floats: separate-map unary weights
 constexpr int kScrDoubles = 136;
 
+// A captured launch sequence of sfseg_power_iterate and what it was captured for (every pointer
+// and parameter the sequence bakes in).
+struct GraphKey {
+    const void* x;
+    const void* f32;
+    const void* fbf;
+    const void* v0;
+    const void* v1;
+    const void* s32;
+    const void* acc;
+    int iters, bf, init;
+    Taps tp;
+};
+struct GraphEntry {
+    GraphKey key;
+    cudaGraphExec_t exec;
+    int64_t launches;
+};
+
 struct sfseg_handle {
     int C = 0;
     double alpha = 1.0, p = 0.1;
@@ -95,6 +114,11 @@ struct sfseg_handle {
     std::vector<cudaEvent_t> ev_free;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pending;
     int64_t timed_launches = 0;
+    // CUDA graphs of sfseg_power_iterate's launch sequence (sfseg_enable_graphs)
+    bool graphs = false;
+    cudaStream_t gstream = nullptr;   // graphs are captured and launched here, ordered by events
+    cudaEvent_t gev[2] = {nullptr, nullptr};
+    std::vector<GraphEntry> gcache;
     // coarse pyramid for sfseg_coarse_start: child handles (C = 1, pooled f) and their x
     std::vector<sfseg_handle*> lvl;
     std::vector<float*> lvl_f, lvl_x;
@@ -110,6 +134,71 @@ static cudaEvent_t take_event(sfseg_handle* h) {
     cudaEvent_t e = nullptr;
     cudaEventCreate(&e);
     return e;
+}
+
+static bool same_key(const GraphKey& a, const GraphKey& b) {
+    return a.x == b.x && a.f32 == b.f32 && a.fbf == b.fbf && a.v0 == b.v0 && a.v1 == b.v1 && a.s32 == b.s32 &&
+           a.acc == b.acc && a.iters == b.iters && a.bf == b.bf && a.init == b.init &&
+           std::memcmp(&a.tp, &b.tp, sizeof(Taps)) == 0;
+}
+
+// Runs `enqueue` (the call's launch sequence) as a CUDA graph on the handle's own stream, ordered
+// after and before the caller's stream by events: replays a graph captured earlier for the same
+// pointers and parameters, or captures one now (at most 8 are kept).  If capture or
+// instantiation fails, the sequence runs directly on the caller's stream instead.
+template <typename F>
+static int run_graph(sfseg_handle* h, cudaStream_t s, float* x, int iters, int bf, int init, const Taps& tp,
+                     double* acc, F&& enqueue) {
+    if (!h->gstream) {
+        SFSEG_CUDA(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
+        SFSEG_CUDA(cudaEventCreateWithFlags(&h->gev[0], cudaEventDisableTiming));
+        SFSEG_CUDA(cudaEventCreateWithFlags(&h->gev[1], cudaEventDisableTiming));
+    }
+    GraphKey key;
+    std::memset(&key, 0, sizeof(key));
+    key.x = x;
+    key.f32 = h->f32;
+    key.fbf = bf > 0 ? (const void*)h->fbf : nullptr;
+    key.v0 = h->vbuf[0];
+    key.v1 = h->vbuf[1];
+    key.s32 = h->sep ? h->s32 : nullptr;
+    key.acc = acc;
+    key.iters = iters;
+    key.bf = bf;
+    key.init = init;
+    key.tp = tp;
+    GraphEntry* hit = nullptr;
+    for (GraphEntry& e : h->gcache)
+        if (same_key(e.key, key)) hit = &e;
+    if (!hit) {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        const int64_t c0 = launches_so_far();
+        bool ok = cudaStreamBeginCapture(h->gstream, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+        int rc = ok ? enqueue(h->gstream) : SFSEG_OK;
+        if (ok) ok = cudaStreamEndCapture(h->gstream, &graph) == cudaSuccess && graph != nullptr;
+        const int64_t n = launches_so_far() - c0;
+        count_launches((int)-n);   // captured, not run
+        if (ok && rc == SFSEG_OK) ok = cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        if (!ok || rc != SFSEG_OK) {
+            cudaGetLastError();
+            return enqueue(s);
+        }
+        if (h->gcache.size() >= 8) {
+            cudaGraphExecDestroy(h->gcache.front().exec);
+            h->gcache.erase(h->gcache.begin());
+        }
+        h->gcache.push_back(GraphEntry{key, exec, n});
+        hit = &h->gcache.back();
+    }
+    SFSEG_CUDA(cudaEventRecord(h->gev[0], s));
+    SFSEG_CUDA(cudaStreamWaitEvent(h->gstream, h->gev[0], 0));
+    SFSEG_CUDA(cudaGraphLaunch(hit->exec, h->gstream));
+    count_launches((int)hit->launches);
+    SFSEG_CUDA(cudaEventRecord(h->gev[1], h->gstream));
+    SFSEG_CUDA(cudaStreamWaitEvent(s, h->gev[1], 0));
+    return SFSEG_OK;
 }
 
 static int check_handle(sfseg_handle* h) {
@@ -255,6 +344,10 @@ int sfseg_destroy(sfseg_handle* h) {
     cudaFree(h->vbuf[1]);
     cudaFree(h->acc);
     cudaFree(h->scratch);
+    for (GraphEntry& e : h->gcache) cudaGraphExecDestroy(e.exec);
+    if (h->gev[0]) cudaEventDestroy(h->gev[0]);
+    if (h->gev[1]) cudaEventDestroy(h->gev[1]);
+    if (h->gstream) cudaStreamDestroy(h->gstream);
     for (float* q : h->adjw) cudaFree(q);
     cudaFree(h->amax);
     cudaFree(h->flags);
@@ -373,41 +466,51 @@ int sfseg_power_iterate(sfseg_handle* h, const void* features, int dtype, const 
         if (int rc = ensure_acc(&h->acc, &h->acc_cap, iters + 2)) return rc;
         acc = h->acc;
     }
-    SFSEG_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (iters + 1), s));
-    const float inv_alpha = (float)(1.0 / h->alpha), p = (float)h->p;
-    const int vt0 = bf > 0 ? kBF16 : kF32;
-    float* last_ckpt = record ? h->ckpt.back() : nullptr;
-    const float* s32 = h->sep ? h->s32 : nullptr;
-    launch_prologue(init, x_inout, h->f32, p, h->g, h->vbuf[0], vt0, record ? h->ckpt[0] : nullptr,
-                    iters == 0 ? x_inout : nullptr, acc, s, s32);
-    SFSEG_LAUNCHED();
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    if (h->timing && iters > 0) {
-        ev0 = take_event(h);
-        ev1 = take_event(h);
-        SFSEG_CUDA(cudaEventRecord(ev0, s));
-    }
-    for (int k = 0; k < iters; ++k) {
-        const bool last = k == iters - 1;
-        const int vin_t = k < bf ? kBF16 : kF32;
-        const int out_t = (k + 1 < bf) ? kBF16 : kF32;
-        const void* fptr = k < bf ? (const void*)h->fbf : (const void*)h->f32;
-        float* ck = nullptr;
-        if (record) {
-            if (last) ck = last_ckpt;
-            else if ((k + 1) % record_every == 0) ck = h->ckpt[(k + 1) / record_every];
-        }
-        launch_iterate(h->vbuf[k & 1], vin_t, last ? (void*)x_inout : h->vbuf[(k + 1) & 1], out_t, last, fptr,
-                       vin_t, ck, h->g, tp, inv_alpha, p, acc + k, acc + k + 1, h->flags, s, s32);
+    // The launch sequence of the call (capturable: no allocation, no host synchronisation).
+    auto enqueue = [&](cudaStream_t st) -> int {
+        SFSEG_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (iters + 1), st));
+        const float inv_alpha = (float)(1.0 / h->alpha), p = (float)h->p;
+        const int vt0 = bf > 0 ? kBF16 : kF32;
+        float* last_ckpt = record ? h->ckpt.back() : nullptr;
+        const float* s32 = h->sep ? h->s32 : nullptr;
+        launch_prologue(init, x_inout, h->f32, p, h->g, h->vbuf[0], vt0, record ? h->ckpt[0] : nullptr,
+                        iters == 0 ? x_inout : nullptr, acc, st, s32);
         SFSEG_LAUNCHED();
+        cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+        if (h->timing && iters > 0) {
+            ev0 = take_event(h);
+            ev1 = take_event(h);
+            SFSEG_CUDA(cudaEventRecord(ev0, st));
+        }
+        for (int k = 0; k < iters; ++k) {
+            const bool last = k == iters - 1;
+            const int vin_t = k < bf ? kBF16 : kF32;
+            const int out_t = (k + 1 < bf) ? kBF16 : kF32;
+            const void* fptr = k < bf ? (const void*)h->fbf : (const void*)h->f32;
+            float* ck = nullptr;
+            if (record) {
+                if (last) ck = last_ckpt;
+                else if ((k + 1) % record_every == 0) ck = h->ckpt[(k + 1) / record_every];
+            }
+            launch_iterate(h->vbuf[k & 1], vin_t, last ? (void*)x_inout : h->vbuf[(k + 1) & 1], out_t, last, fptr,
+                           vin_t, ck, h->g, tp, inv_alpha, p, acc + k, acc + k + 1, h->flags, st, s32);
+            SFSEG_LAUNCHED();
+        }
+        if (ev1) {
+            SFSEG_CUDA(cudaEventRecord(ev1, st));
+            h->ev_pending.emplace_back(ev0, ev1);
+            h->timed_launches += iters;
+        }
+        launch_scale_inv_norm(x_inout, h->N, acc + iters, h->flags, st);
+        SFSEG_LAUNCHED();
+        return SFSEG_OK;
+    };
+    const bool graphable = h->graphs && !record && !norms_out && !h->timing && features == nullptr;
+    if (graphable) {
+        if (int rc = run_graph(h, s, x_inout, iters, bf, init, tp, acc, enqueue)) return rc;
+    } else if (int rc = enqueue(s)) {
+        return rc;
     }
-    if (ev1) {
-        SFSEG_CUDA(cudaEventRecord(ev1, s));
-        h->ev_pending.emplace_back(ev0, ev1);
-        h->timed_launches += iters;
-    }
-    launch_scale_inv_norm(x_inout, h->N, acc + iters, h->flags, s);
-    SFSEG_LAUNCHED();
     if (record) {
         h->rec_K = iters;
         h->rec_every = record_every;
@@ -419,6 +522,12 @@ int sfseg_power_iterate(sfseg_handle* h, const void* features, int dtype, const 
         if (int rc = read_flags(h, s)) return rc;
         for (int k = 0; k < iters; ++k) norms_out[k] = std::sqrt(a[k + 1]);
     }
+    return SFSEG_OK;
+}
+
+int sfseg_enable_graphs(sfseg_handle* h, int on) {
+    if (int rc = check_handle(h)) return rc;
+    h->graphs = on != 0;
     return SFSEG_OK;
 }
 

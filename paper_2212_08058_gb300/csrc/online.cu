@@ -43,6 +43,7 @@ int sfseg_online_create(const sfseg_params* prm, int C, int q, int H, int W, sfs
     if (q < 1 || q > 4096) return set_last_error(SFSEG_ERR_INVALID_ARG, "window length q must be in [1, 4096]");
     sfseg_handle* h = nullptr;
     if (int rc = sfseg_create(prm, C, q, H, W, &h)) return rc;
+    sfseg_enable_graphs(h, 1);   // the window's iterations replay as CUDA graphs (two buffer parities)
     sfseg_online* o = new sfseg_online();
     o->h = h;
     o->C = C;

@@ -67,6 +67,7 @@ SIGNATURES = {
     "sfseg_coarse_start": [_vp, ctypes.POINTER(Neighborhood), _i, ctypes.c_double, _i, _i, _vp,
                            ctypes.POINTER(_i), _vp],
     "sfseg_selftest_wait": [_vp, ctypes.c_longlong, _vp],
+    "sfseg_enable_graphs": [_vp, _i],
     "sfseg_enable_iter_timing": [_vp, _i],
     "sfseg_iter_timing": [_vp, _dp, ctypes.POINTER(ctypes.c_int64)],
     "sfseg_kernel_launches": [ctypes.POINTER(ctypes.c_int64)],
@@ -313,6 +314,10 @@ class PowerIteration:
         """Run the bounded-wait failure path on purpose (sfseg_selftest_wait); raises SFSegError
         with status TIMEOUT, which is the expected outcome."""
         _check(lib().sfseg_selftest_wait(self._h, int(spins), _stream()))
+
+    def enable_graphs(self, on: bool = True):
+        """Run feature-less power_iterate calls as replayed CUDA graphs (sfseg_enable_graphs)."""
+        _check(lib().sfseg_enable_graphs(self._h, int(bool(on))))
 
     def enable_iter_timing(self, on: bool = True):
         _check(lib().sfseg_enable_iter_timing(self._h, int(bool(on))))

@@ -279,3 +279,32 @@ def test_bounded_wait_reports_timeout():
         x = h.power_iterate(torch.from_numpy(V).cuda(), radius=(1, 3, 3), iters=8).cpu().numpy()
     xo, _ = _oracle(V, (1, 3, 3), 8)
     assert np.abs(x - xo).max() <= TOL_F32
+
+
+def test_cuda_graph_replay_is_identical():
+    """sfseg_enable_graphs: calls replayed from captured CUDA graphs give bit-identical results
+    to direct launches -- with new feature values under the same pointers, new x buffers (new
+    captures), more keys than the cache holds, a bf16 phase and the S_m start."""
+    sf = _sf()
+    T, H, W = 8, 64, 64
+    V1 = torch.from_numpy(synth.drifting_blob(T, H, W, seed=7600)).cuda()
+    V2 = torch.from_numpy(synth.drifting_blob(T, H, W, seed=7601)).cuda()
+    with sf.PowerIteration(1, T, H, W) as ref, sf.PowerIteration(1, T, H, W) as gr:
+        gr.enable_graphs(True)
+        xs = [torch.empty((T, H, W), device="cuda") for _ in range(10)]
+        for V in (V1, V2, V1):
+            ref.set_features(V)
+            gr.set_features(V)
+            for i, (radius, iters, nb, init) in enumerate([((1, 3, 3), 20, 0, "uniform"), ((2, 7, 7), 7, 3, "uniform"),
+                                                           ((1, 3, 3), 5, 0, "smap"), ((1, 2, 3), 4, 0, "uniform")]):
+                a = ref.power_iterate(None, radius=radius, iters=iters, iters_bf16=nb, init=init)
+                b = gr.power_iterate(None, radius=radius, iters=iters, iters_bf16=nb, init=init, x=xs[i])
+                torch.cuda.synchronize()
+                assert torch.equal(a, b), (radius, iters, nb, init)
+        # more distinct keys than the cache keeps (x buffers), each replayed twice
+        for rep in range(2):
+            for i in range(10):
+                b = gr.power_iterate(None, radius=(1, 3, 3), iters=3 + i % 3, x=xs[i])
+                a = ref.power_iterate(None, radius=(1, 3, 3), iters=3 + i % 3)
+                torch.cuda.synchronize()
+                assert torch.equal(a, b)
