@@ -308,3 +308,37 @@ def test_cuda_graph_replay_is_identical():
                 a = ref.power_iterate(None, radius=(1, 3, 3), iters=3 + i % 3)
                 torch.cuda.synchronize()
                 assert torch.equal(a, b)
+
+
+def test_near_maximum_volume_sampled():
+    """Close to the largest volume a handle takes (T H W < 2^31; here 996 x 1080 x 1990 = 2.14e9
+    voxels, whose pitched layout, 2.17e9 elements, passes 2^31): y = A x at radius (2,7,7)
+    through the TMA kernel, checked at sampled voxels (corners, borders, interior) against the
+    FP64 oracle evaluated on the crop that holds each voxel's whole neighbourhood.  Inputs are
+    drawn on the device from a seeded generator."""
+    sf = _sf()
+    T, H, W = 996, 1080, 1990
+    r = (2, 7, 7)
+    gen = torch.Generator(device="cuda").manual_seed(7700)
+    feats = torch.rand((1, T, H, W), device="cuda", generator=gen)
+    x = torch.rand((T, H, W), device="cuda", generator=gen) + 0.5
+    with sf.PowerIteration(1, T, H, W) as h:
+        h.set_features(feats)
+        y = h.apply(x, r)
+        torch.cuda.synchronize()
+        rng = np.random.default_rng(17)
+        pts = [(0, 0, 0), (T - 1, H - 1, W - 1), (0, H - 1, 0), (T - 1, 0, W - 1), (T // 2, 7, W - 8)]
+        pts += [tuple(int(v) for v in rng.integers((0, 0, 0), (T, H, W))) for _ in range(11)]
+        scale = float(y.abs().max())
+        for (t, hh, w) in pts:
+            sl = tuple(slice(max(c - rr, 0), min(c + rr + 1, n)) for c, rr, n in zip((t, hh, w), r, (T, H, W)))
+            fc = feats[0][sl].cpu().numpy().astype(np.float64)
+            xc = x[sl].cpu().numpy().astype(np.float64)
+            yo = oracle.filter_apply(fc, fc, 0.1, 1.0, r, xc)
+            ci = tuple(c - s.start for c, s in zip((t, hh, w), sl))
+            assert abs(float(y[t, hh, w]) - yo[ci]) <= 1e-5 * scale, ((t, hh, w), float(y[t, hh, w]), yo[ci])
+        # one power iteration at this size runs and stays finite
+        xs = h.power_iterate(None, radius=r, iters=2)
+        assert bool(torch.isfinite(xs[::97, ::101, ::103]).all())
+    del feats, x, y, xs
+    torch.cuda.empty_cache()
