@@ -39,8 +39,8 @@ typedef enum sfseg_status {
     SFSEG_ERR_DTYPE = 3,       /* unknown dtype code */
     SFSEG_ERR_CUDA = 4,        /* a CUDA runtime call failed (message holds the CUDA error) */
     SFSEG_ERR_OOM = 5,         /* device allocation failed */
-    SFSEG_ERR_TIMEOUT = 6,     /* a bounded device-side wait (TMA copy) gave up; reported by the
-                                  next synchronising call */
+    SFSEG_ERR_TIMEOUT = 6,     /* a bounded device-side wait (for a TMA copy or an MMA) gave up;
+                                  reported by the next synchronising call */
     SFSEG_ERR_NONFINITE = 7,   /* a feature is negative, NaN or Inf, or a norm became non-finite */
     SFSEG_ERR_ZERO_NORM = 8,   /* an iterate became exactly zero (e.g. u = 0 everywhere) */
     SFSEG_ERR_STATE = 9,       /* call order violated (no features set, no recorded forward, ...) */
