@@ -110,7 +110,7 @@ __global__ void adjoint_prep_kernel(const float* xk, const double* acc_k, const 
     const float sk = inv_norm_from(acc_k, flags), sn = inv_norm_from(acc_n, flags);
     const float dotn = (float)*dot_n;
     for_each_voxel(g, [&](int64_t, int64_t j) {
-        const float u = unary_pow(f[j], p);
+        const float u = unary_pow_fast(f[j], p);
         vx[j] = u * (sk * xk[j]);
         vg[j] = u * ((gn[j] - sn * xn[j] * dotn) * sn);
     });
@@ -125,7 +125,7 @@ __global__ void adjoint_combine_kernel(const float* xk, const double* acc_k, con
     float part = 0.f;
     for_each_voxel(g, [&](int64_t, int64_t j) {
         const float fv = f[j];
-        const float u = unary_pow(fv, p);
+        const float u = unary_pow_fast(fv, p);
         const float x = sk * xk[j];
         const float gy = (gn[j] - sn * xn[j] * dotn) * sn;
         part += x * gk[j];
@@ -155,7 +155,7 @@ bool launch_adjoint_step_fast(const float* xk, const double* acc_k, const float*
 
 // v = u x, both in the internal layout.
 __global__ void state_internal_kernel(const float* x, const float* f, float p, Geom g, float* v) {
-    for_each_voxel(g, [&](int64_t, int64_t j) { v[j] = unary_pow(f[j], p) * x[j]; });
+    for_each_voxel(g, [&](int64_t, int64_t j) { v[j] = unary_pow_fast(f[j], p) * x[j]; });
 }
 
 bool launch_apply_internal_fast(const float* x, float* y, float* v, const float* f32, Geom g, const Taps& tp,
