@@ -344,6 +344,7 @@ def bench_adjoint(sfseg, synth, steps: int = 5):
     tgt = torch.from_numpy((m > 0.5).astype("float32")).cuda()
     w = (w * 8.0).astype("float32")
     h = sfseg.PowerIteration(8, Tb, Hb, Wb)
+    h.enable_graphs(True)          # the backward pass replays as a CUDA graph
     x = torch.empty((Tb, Hb, Wb), device="cuda")
 
     def run():

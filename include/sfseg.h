@@ -279,9 +279,10 @@ int sfseg_selftest_wait(sfseg_handle* h, long long spins, void* stream);
 
 /* CUDA graphs for launch-bound calls (no counterpart in the paper).  When enabled, a call of
  * sfseg_power_iterate that passes features == NULL (features already set), records nothing,
- * asks for no norms and is not being timed runs its launch sequence as a CUDA graph: the first
- * call for given pointers and parameters (x_inout, iters, iters_bf16, init, neighbourhood, the
- * handle's buffers) captures it, later ones replay it.  The graph runs on a stream of the handle,
+ * asks for no norms and is not being timed, and every sfseg_backward, run their launch
+ * sequences as CUDA graphs: the first call for given pointers and parameters (x_inout or
+ * grad_x, iters, iters_bf16, init, the recording, neighbourhood, the handle's buffers) captures
+ * it, later ones replay it.  The graph runs on a stream of the handle,
  * ordered after the work already queued on the caller's stream and before the work queued
  * after the call; results are identical.  Worth it for small volumes, where launch latency
  * dominates.  Off by default. */

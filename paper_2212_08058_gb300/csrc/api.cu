@@ -60,6 +60,7 @@ constexpr int kScrDoubles = 136;
 // A captured launch sequence of sfseg_power_iterate and what it was captured for (every pointer
 // and parameter the sequence bakes in).
 struct GraphKey {
+    int kind;   // 0: sfseg_power_iterate, 1: sfseg_backward
     const void* x;
     const void* f32;
     const void* fbf;
@@ -137,7 +138,7 @@ static cudaEvent_t take_event(sfseg_handle* h) {
 }
 
 static bool same_key(const GraphKey& a, const GraphKey& b) {
-    return a.x == b.x && a.f32 == b.f32 && a.fbf == b.fbf && a.v0 == b.v0 && a.v1 == b.v1 && a.s32 == b.s32 &&
+    return a.kind == b.kind && a.x == b.x && a.f32 == b.f32 && a.fbf == b.fbf && a.v0 == b.v0 && a.v1 == b.v1 && a.s32 == b.s32 &&
            a.acc == b.acc && a.iters == b.iters && a.bf == b.bf && a.init == b.init &&
            std::memcmp(&a.tp, &b.tp, sizeof(Taps)) == 0;
 }
@@ -147,26 +148,12 @@ static bool same_key(const GraphKey& a, const GraphKey& b) {
 // pointers and parameters, or captures one now (at most 8 are kept).  If capture or
 // instantiation fails, the sequence runs directly on the caller's stream instead.
 template <typename F>
-static int run_graph(sfseg_handle* h, cudaStream_t s, float* x, int iters, int bf, int init, const Taps& tp,
-                     double* acc, F&& enqueue) {
+static int run_graph(sfseg_handle* h, cudaStream_t s, const GraphKey& key, F&& enqueue) {
     if (!h->gstream) {
         SFSEG_CUDA(cudaStreamCreateWithFlags(&h->gstream, cudaStreamNonBlocking));
         SFSEG_CUDA(cudaEventCreateWithFlags(&h->gev[0], cudaEventDisableTiming));
         SFSEG_CUDA(cudaEventCreateWithFlags(&h->gev[1], cudaEventDisableTiming));
     }
-    GraphKey key;
-    std::memset(&key, 0, sizeof(key));
-    key.x = x;
-    key.f32 = h->f32;
-    key.fbf = bf > 0 ? (const void*)h->fbf : nullptr;
-    key.v0 = h->vbuf[0];
-    key.v1 = h->vbuf[1];
-    key.s32 = h->sep ? h->s32 : nullptr;
-    key.acc = acc;
-    key.iters = iters;
-    key.bf = bf;
-    key.init = init;
-    key.tp = tp;
     GraphEntry* hit = nullptr;
     for (GraphEntry& e : h->gcache)
         if (same_key(e.key, key)) hit = &e;
@@ -507,7 +494,21 @@ int sfseg_power_iterate(sfseg_handle* h, const void* features, int dtype, const 
     };
     const bool graphable = h->graphs && !record && !norms_out && !h->timing && features == nullptr;
     if (graphable) {
-        if (int rc = run_graph(h, s, x_inout, iters, bf, init, tp, acc, enqueue)) return rc;
+        GraphKey key;
+        std::memset(&key, 0, sizeof(key));
+        key.kind = 0;
+        key.x = x_inout;
+        key.f32 = h->f32;
+        key.fbf = bf > 0 ? (const void*)h->fbf : nullptr;
+        key.v0 = h->vbuf[0];
+        key.v1 = h->vbuf[1];
+        key.s32 = h->sep ? h->s32 : nullptr;
+        key.acc = acc;
+        key.iters = iters;
+        key.bf = bf;
+        key.init = init;
+        key.tp = tp;
+        if (int rc = run_graph(h, s, key, enqueue)) return rc;
     } else if (int rc = enqueue(s)) {
         return rc;
     }
@@ -632,43 +633,65 @@ int sfseg_backward(sfseg_handle* h, const sfseg_neighborhood* nb, const float* g
         h->seg.push_back(q);
     }
     if (int rc = ensure_acc(&h->dots, &h->dots_cap, K + 2)) return rc;
-    SFSEG_CUDA(cudaMemsetAsync(h->gz, 0, sizeof(float) * h->NP, s));
-    SFSEG_CUDA(cudaMemsetAsync(h->dots, 0, sizeof(double) * (K + 1), s));
-    SFSEG_CUDA(cudaMemsetAsync(h->scratch, 0, sizeof(double) * kScrDoubles, s));
-    float* xK = h->ckpt.back();
-    launch_grad_in(grad_x, xK, h->rec_acc + K, h->gbuf[0], h->g, h->dots + K, s);
-    SFSEG_LAUNCHED();
-    int gi = 0;   // gbuf[gi] holds g_{k+1}
-    const int nseg = (K + c - 1) / c;
-    for (int sgi = nseg - 1; sgi >= 0; --sgi) {
-        const int k0 = sgi * c, k1 = (k0 + c < K) ? k0 + c : K;
-        std::vector<const float*> xs((size_t)(k1 - k0 + 1));
-        xs[0] = h->ckpt[sgi];
-        for (int i = 1; i <= k1 - k0; ++i) {
-            if (k0 + i == K) {
-                xs[i] = xK;
-            } else {   // recompute x~_{k0+i} = A x_{k0+i-1} from the recorded norm
-                if (!(fast_adj && launch_apply_internal_fast(xs[i - 1], h->seg[i], h->adjw[0], h->f32, h->g, tp,
-                                                             inv_alpha, p, h->rec_acc + k0 + i - 1, h->flags, s)))
-                    launch_apply(xs[i - 1], h->g.pitch, h->seg[i], h->g.pitch, h->f32, h->g, tp, inv_alpha, p,
-                                 h->rec_acc + k0 + i - 1, h->scratch + kScrApplyAcc, h->flags, s);
+    // The launch sequence of the reverse pass (capturable: no allocation, no host synchronisation).
+    auto enqueue = [&](cudaStream_t st) -> int {
+        SFSEG_CUDA(cudaMemsetAsync(h->gz, 0, sizeof(float) * h->NP, st));
+        SFSEG_CUDA(cudaMemsetAsync(h->dots, 0, sizeof(double) * (K + 1), st));
+        SFSEG_CUDA(cudaMemsetAsync(h->scratch, 0, sizeof(double) * kScrDoubles, st));
+        float* xK = h->ckpt.back();
+        launch_grad_in(grad_x, xK, h->rec_acc + K, h->gbuf[0], h->g, h->dots + K, st);
+        SFSEG_LAUNCHED();
+        int gi = 0;   // gbuf[gi] holds g_{k+1}
+        const int nseg = (K + c - 1) / c;
+        for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+            const int k0 = sgi * c, k1 = (k0 + c < K) ? k0 + c : K;
+            std::vector<const float*> xs((size_t)(k1 - k0 + 1));
+            xs[0] = h->ckpt[sgi];
+            for (int i = 1; i <= k1 - k0; ++i) {
+                if (k0 + i == K) {
+                    xs[i] = xK;
+                } else {   // recompute x~_{k0+i} = A x_{k0+i-1} from the recorded norm
+                    if (!(fast_adj && launch_apply_internal_fast(xs[i - 1], h->seg[i], h->adjw[0], h->f32, h->g, tp,
+                                                                 inv_alpha, p, h->rec_acc + k0 + i - 1, h->flags, st)))
+                        launch_apply(xs[i - 1], h->g.pitch, h->seg[i], h->g.pitch, h->f32, h->g, tp, inv_alpha, p,
+                                     h->rec_acc + k0 + i - 1, h->scratch + kScrApplyAcc, h->flags, st);
+                    SFSEG_LAUNCHED();
+                    xs[i] = h->seg[i];
+                }
+            }
+            for (int k = k1 - 1; k >= k0; --k) {
+                float* gnext = k > 0 ? h->gbuf[gi ^ 1] : nullptr;
+                if (!(fast_adj && launch_adjoint_step_fast(xs[k - k0], h->rec_acc + k, xs[k + 1 - k0], h->rec_acc + k + 1,
+                                                           h->gbuf[gi], h->dots + k + 1, gnext, h->dots + k, h->gz,
+                                                           h->f32, h->g, tp, inv_alpha, p, h->adjw, h->flags, st)))
+                    launch_adjoint_step(xs[k - k0], h->rec_acc + k, xs[k + 1 - k0], h->rec_acc + k + 1, h->gbuf[gi],
+                                        h->dots + k + 1, gnext, h->dots + k, h->gz, h->f32, h->g, tp, inv_alpha, p, st);
                 SFSEG_LAUNCHED();
-                xs[i] = h->seg[i];
+                gi ^= 1;
             }
         }
-        for (int k = k1 - 1; k >= k0; --k) {
-            float* gnext = k > 0 ? h->gbuf[gi ^ 1] : nullptr;
-            if (!(fast_adj && launch_adjoint_step_fast(xs[k - k0], h->rec_acc + k, xs[k + 1 - k0], h->rec_acc + k + 1,
-                                                       h->gbuf[gi], h->dots + k + 1, gnext, h->dots + k, h->gz,
-                                                       h->f32, h->g, tp, inv_alpha, p, h->adjw, h->flags, s)))
-                launch_adjoint_step(xs[k - k0], h->rec_acc + k, xs[k + 1 - k0], h->rec_acc + k + 1, h->gbuf[gi],
-                                    h->dots + k + 1, gnext, h->dots + k, h->gz, h->f32, h->g, tp, inv_alpha, p, s);
-            SFSEG_LAUNCHED();
-            gi ^= 1;
-        }
+        launch_weight_grad(h->feat_ptr, h->feat_dtype, h->C, h->g, h->gz, h->scratch + kScrWeightGrad, st);
+        SFSEG_LAUNCHED();
+        return SFSEG_OK;
+    };
+    if (h->graphs) {
+        GraphKey key;
+        std::memset(&key, 0, sizeof(key));
+        key.kind = 1;
+        key.x = grad_x;
+        key.f32 = h->f32;
+        key.fbf = h->feat_ptr;
+        key.v0 = h->ckpt[0];
+        key.v1 = h->gz;
+        key.acc = h->rec_acc;
+        key.iters = K;
+        key.bf = c;
+        key.init = h->feat_dtype;
+        key.tp = tp;
+        if (int rc = run_graph(h, s, key, enqueue)) return rc;
+    } else if (int rc = enqueue(s)) {
+        return rc;
     }
-    launch_weight_grad(h->feat_ptr, h->feat_dtype, h->C, h->g, h->gz, h->scratch + kScrWeightGrad, s);
-    SFSEG_LAUNCHED();
     std::vector<double> wacc((size_t)h->C + 1);
     SFSEG_CUDA(cudaMemcpyAsync(wacc.data(), h->scratch + kScrWeightGrad, sizeof(double) * (h->C + 1),
                                cudaMemcpyDeviceToHost, s));

@@ -166,3 +166,32 @@ def test_adjoint_with_the_maximum_channel_count():
     scale = max(np.abs(gwo).max(), abs(gbo))
     assert np.abs(gw - gwo).max() <= 2e-4 * scale
     assert abs(gb - gbo) <= 2e-4 * scale
+
+
+def test_adjoint_graph_replay_is_identical():
+    """sfseg_backward replayed from a captured CUDA graph (sfseg_enable_graphs) gives the same
+    weight gradients as direct launches (to the order of the FP64 atomic sums), over repeated forward/backward calls with new loss
+    gradients under the same pointers."""
+    sf = _sf()
+    V, _, w = synth.multichannel(6, 40, 70, C=4, seed=4010)
+    feats = torch.from_numpy(V).cuda()
+    rng = np.random.default_rng(21)
+    outs = {}
+    for on in (False, True):
+        with sf.PowerIteration(4, 6, 40, 70) as h:
+            h.enable_graphs(on)
+            g = torch.empty((6, 40, 70), device="cuda")
+            res = []
+            for rep in range(3):
+                x = h.power_iterate(feats, w, 0.2, (1, 3, 3), iters=12, record_every=4)
+                g.copy_(torch.from_numpy(rng.normal(size=(6, 40, 70)).astype(np.float32) if not on else
+                                         outs["g"][rep]))
+                if not on:
+                    outs.setdefault("g", []).append(g.cpu().numpy().copy())
+                gw, gb = h.backward(g, (1, 3, 3))
+                res.append((gw.copy(), gb))
+            outs[on] = res
+    # the FP64 sums are accumulated with atomics, so their order (not the arithmetic) may differ
+    for (a, ab), (b, bb) in zip(outs[False], outs[True]):
+        np.testing.assert_allclose(a, b, rtol=1e-6, atol=1e-9 * np.abs(a).max())
+        assert abs(ab - bb) <= 1e-6 * max(abs(ab), np.abs(a).max())

