@@ -446,6 +446,18 @@ def bench_time_to_residual(sfseg, synth, warmstart, tol: float = 1e-4):
     return res
 
 
+EXTRAS = {
+    "bf16_multichannel": lambda sf, sy: bench_bf16_multichannel(sf, sy),
+    "soft_binarize": lambda sf, sy: bench_soft_binarize(sf, sy),
+    "online": lambda sf, sy: bench_online(sf, sy),
+    "separate_maps": lambda sf, sy: bench_separate_maps(sf, sy),
+    "adjoint": lambda sf, sy: bench_adjoint(sf, sy, steps=1),
+    "small_graphs": lambda sf, sy: bench_small_graphs(sf, sy),
+    "r133_storage": lambda sf, sy: bench_r133_storage(sf, sy, steps=2),
+    "time_to_residual": lambda sf, sy, ws: bench_time_to_residual(sf, sy, ws),
+}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -454,7 +466,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the bf16 and time-to-residual lines")
+    ap.add_argument("--only", choices=sorted(EXTRAS), help="run one extra measurement alone and print its JSON "
+                    "(for profiling that part)")
     args = ap.parse_args()
+    if args.only:
+        from paper_2212_08058_gb300 import build, sfseg, synth, warmstart
+        build.build()
+        fn = EXTRAS[args.only]
+        res = fn(sfseg, synth, warmstart) if args.only == "time_to_residual" else fn(sfseg, synth)
+        print(json.dumps({"only": args.only, **res}), flush=True)
+        return
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     rank = int(os.environ.get("RANK", "0"))
