@@ -641,8 +641,42 @@ int sfseg_backward(sfseg_handle* h, const sfseg_neighborhood* nb, const float* g
         float* xK = h->ckpt.back();
         launch_grad_in(grad_x, xK, h->rec_acc + K, h->gbuf[0], h->g, h->dots + K, st);
         SFSEG_LAUNCHED();
-        int gi = 0;   // gbuf[gi] holds g_{k+1}
         const int nseg = (K + c - 1) / c;
+        if (fast_adj) {
+            // State form on the TMA kernel: V_k in seg[k - k0], Q_x in adjw[0], Q_g in adjw[1], v_g
+            // alternating between adjw[2] and adjw[3], G_k in gbuf[1]; dots[k] = sum V_k B (k < K).
+            float* vg_cur = h->adjw[2];
+            float* vg_nxt = h->adjw[3];
+            launch_adjoint_first(xK, h->rec_acc + K, h->gbuf[0], h->dots + K, h->f32, p, h->g, vg_cur, st);
+            SFSEG_LAUNCHED();
+            for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+                const int k0 = sgi * c, k1 = (k0 + c < K) ? k0 + c : K;
+                launch_state_internal(h->ckpt[sgi], h->f32, p, h->g, h->seg[0], st);
+                SFSEG_LAUNCHED();
+                for (int i = 1; i < k1 - k0; ++i) {   // V_{k0+i}: the plain step from the recorded norm
+                    if (!launch_iterate_fast(h->seg[i - 1], kF32, h->seg[i], kF32, false, h->f32, h->g, tp, inv_alpha,
+                                             p, h->rec_acc + k0 + i - 1, nullptr, h->flags, st))
+                        return fail(SFSEG_ERR_CUDA, "the TMA stencil could not be launched");
+                    SFSEG_LAUNCHED();
+                }
+                for (int k = k1 - 1; k >= k0; --k) {
+                    const float* Vk = h->seg[k - k0];
+                    if (!launch_filter_fast(Vk, 1, h->adjw[0], nullptr, h->f32, h->g, tp, inv_alpha, p,
+                                            h->rec_acc + k, h->flags, st) ||
+                        !launch_adjoint_gpass_fast(vg_cur, h->gbuf[1], h->adjw[1], Vk, h->f32, h->g, tp, inv_alpha, p,
+                                                   h->dots + k, h->flags, st))
+                        return fail(SFSEG_ERR_CUDA, "the TMA stencil could not be launched");
+                    launch_adjoint_combine_state(h->f32, vg_cur, h->adjw[0], Vk, h->adjw[1], h->gbuf[1],
+                                                 h->rec_acc + k, h->dots + k, h->g, h->gz, k > 0 ? vg_nxt : nullptr, st);
+                    SFSEG_LAUNCHED();
+                    std::swap(vg_cur, vg_nxt);
+                }
+            }
+            launch_weight_grad(h->feat_ptr, h->feat_dtype, h->C, h->g, h->gz, h->scratch + kScrWeightGrad, st);
+            SFSEG_LAUNCHED();
+            return SFSEG_OK;
+        }
+        int gi = 0;   // gbuf[gi] holds g_{k+1}
         for (int sgi = nseg - 1; sgi >= 0; --sgi) {
             const int k0 = sgi * c, k1 = (k0 + c < K) ? k0 + c : K;
             std::vector<const float*> xs((size_t)(k1 - k0 + 1));
@@ -651,21 +685,16 @@ int sfseg_backward(sfseg_handle* h, const sfseg_neighborhood* nb, const float* g
                 if (k0 + i == K) {
                     xs[i] = xK;
                 } else {   // recompute x~_{k0+i} = A x_{k0+i-1} from the recorded norm
-                    if (!(fast_adj && launch_apply_internal_fast(xs[i - 1], h->seg[i], h->adjw[0], h->f32, h->g, tp,
-                                                                 inv_alpha, p, h->rec_acc + k0 + i - 1, h->flags, st)))
-                        launch_apply(xs[i - 1], h->g.pitch, h->seg[i], h->g.pitch, h->f32, h->g, tp, inv_alpha, p,
-                                     h->rec_acc + k0 + i - 1, h->scratch + kScrApplyAcc, h->flags, st);
+                    launch_apply(xs[i - 1], h->g.pitch, h->seg[i], h->g.pitch, h->f32, h->g, tp, inv_alpha, p,
+                                 h->rec_acc + k0 + i - 1, h->scratch + kScrApplyAcc, h->flags, st);
                     SFSEG_LAUNCHED();
                     xs[i] = h->seg[i];
                 }
             }
             for (int k = k1 - 1; k >= k0; --k) {
                 float* gnext = k > 0 ? h->gbuf[gi ^ 1] : nullptr;
-                if (!(fast_adj && launch_adjoint_step_fast(xs[k - k0], h->rec_acc + k, xs[k + 1 - k0], h->rec_acc + k + 1,
-                                                           h->gbuf[gi], h->dots + k + 1, gnext, h->dots + k, h->gz,
-                                                           h->f32, h->g, tp, inv_alpha, p, h->adjw, h->flags, st)))
-                    launch_adjoint_step(xs[k - k0], h->rec_acc + k, xs[k + 1 - k0], h->rec_acc + k + 1, h->gbuf[gi],
-                                        h->dots + k + 1, gnext, h->dots + k, h->gz, h->f32, h->g, tp, inv_alpha, p, st);
+                launch_adjoint_step(xs[k - k0], h->rec_acc + k, xs[k + 1 - k0], h->rec_acc + k + 1, h->gbuf[gi],
+                                    h->dots + k + 1, gnext, h->dots + k, h->gz, h->f32, h->g, tp, inv_alpha, p, st);
                 SFSEG_LAUNCHED();
                 gi ^= 1;
             }

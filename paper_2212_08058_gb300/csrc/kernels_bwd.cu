@@ -99,72 +99,64 @@ void launch_adjoint_step(const float* xk, const double* acc_k, const float* xn, 
     run_stencil(op, tp, 8, nullptr, dot_k, nullptr, nullptr, s);
 }
 
-// ---- the same step on the TMA kernel: two filtering passes instead of one six-signal pass.
-// With Q = a1 c0 - p c1 + a3 c2 (kernels_fast.cu, MODE 1/2) for the signals of u x (Q_x) and of
-// u g_y (Q_g), the feature term above is (1 - f) u (g_y Q_x + x Q_g), and g_k = A g_y.
-
-// v_x = u x_k, v_g = u g_y (internal layout).
-__global__ void adjoint_prep_kernel(const float* xk, const double* acc_k, const float* xn, const double* acc_n,
-                                    const float* gn, const double* dot_n, const float* f, float p, Geom g, float* vx,
-                                    float* vg, int* flags) {
-    const float sk = inv_norm_from(acc_k, flags), sn = inv_norm_from(acc_n, flags);
-    const float dotn = (float)*dot_n;
-    for_each_voxel(g, [&](int64_t, int64_t j) {
-        const float u = unary_pow_fast(f[j], p);
-        vx[j] = u * (sk * xk[j]);
-        vg[j] = u * ((gn[j] - sn * xn[j] * dotn) * sn);
-    });
-}
-
-// gz += (1 - f) u (g_y Q_x + x Q_g), dot_k += <x_k, g_k>.
-__global__ void adjoint_combine_kernel(const float* xk, const double* acc_k, const float* xn, const double* acc_n,
-                                       const float* gn, const double* dot_n, const float* f, float p, Geom g,
-                                       const float* qx, const float* qg, const float* gk, float* gz, double* dot_k) {
-    const float sk = inv_norm_from(acc_k, nullptr), sn = inv_norm_from(acc_n, nullptr);
-    const float dotn = (float)*dot_n;
-    float part = 0.f;
-    for_each_voxel(g, [&](int64_t, int64_t j) {
-        const float fv = f[j];
-        const float u = unary_pow_fast(fv, p);
-        const float x = sk * xk[j];
-        const float gy = (gn[j] - sn * xn[j] * dotn) * sn;
-        part += x * gk[j];
-        gz[j] += (1.f - fv) * u * (gy * qx[j] + x * qg[j]);
-    });
-    const double b = block_sum((double)part);
-    if (threadIdx.x == 0) atomicAdd(dot_k, b);
-}
-
-bool launch_adjoint_step_fast(const float* xk, const double* acc_k, const float* xn, const double* acc_n,
-                              const float* gn, const double* dot_n, float* gk_out, double* dot_k, float* gz,
-                              const float* f32, Geom g, const Taps& tp, float inv_alpha, float p, float* const work[4],
-                              int* flags, cudaStream_t s) {
-    if (!fast_iterate_supported(tp)) return false;
-    const RowLaunch rl = row_launch(g, num_sms(), 8);
-    adjoint_prep_kernel<<<rl.blocks, rl.threads, 0, s>>>(xk, acc_k, xn, acc_n, gn, dot_n, f32, p, g, work[0], work[1],
-                                                         flags);
-    count_launches(1);
-    if (!launch_filter_fast(work[0], 1, work[2], nullptr, f32, g, tp, inv_alpha, p, nullptr, flags, s)) return false;
-    float* gk = gk_out ? gk_out : work[0];   // v_x is consumed by now
-    if (!launch_filter_fast(work[1], 2, gk, work[3], f32, g, tp, inv_alpha, p, nullptr, flags, s)) return false;
-    adjoint_combine_kernel<<<rl.blocks, rl.threads, 0, s>>>(xk, acc_k, xn, acc_n, gn, dot_n, f32, p, g, work[2],
-                                                            work[3], gk, gz, dot_k);
-    count_launches(1);
-    return true;
-}
-
 // v = u x, both in the internal layout.
 __global__ void state_internal_kernel(const float* x, const float* f, float p, Geom g, float* v) {
     for_each_voxel(g, [&](int64_t, int64_t j) { v[j] = unary_pow_fast(f[j], p) * x[j]; });
 }
 
-bool launch_apply_internal_fast(const float* x, float* y, float* v, const float* f32, Geom g, const Taps& tp,
-                                float inv_alpha, float p, const double* acc_in, int* flags, cudaStream_t s) {
-    if (!fast_iterate_supported(tp)) return false;
+
+// ---- the reverse step in the stencil's state form (TMA kernel only).  With V_k = u x~_k (the
+// state the forward step itself carries), G_k = u g_k and v_g = u g_y, a step is: Q_x from V_k
+// (mode 1, scaled by s_k = 1/||x~_k||), the g-pass on v_g (mode 5: G_k, Q_g and sum V_k B), and
+// one element-wise pass that adds the feature term and forms the next step's v_g.  The
+// recomputation between checkpoints is the plain step on V (mode 0).
+
+// v_g of the first reverse step: u g_y = s_K u (g_K - s_K x~_K <x_K, g_K>).
+__global__ void adjoint_first_kernel(const float* xK, const double* accK, const float* gK, const double* dotK,
+                                     const float* f, float p, Geom g, float* vg) {
+    const float sK = inv_norm_from(accK, nullptr);
+    const float d = (float)*dotK;
+    for_each_voxel(g, [&](int64_t, int64_t j) {
+        vg[j] = unary_pow_fast(f[j], p) * ((gK[j] - sK * xK[j] * d) * sK);
+    });
+}
+
+void launch_adjoint_first(const float* xK, const double* accK, const float* gK, const double* dotK,
+                          const float* f32, float p, Geom g, float* vg, cudaStream_t s) {
+    const RowLaunch rl = row_launch(g, num_sms(), 8);
+    adjoint_first_kernel<<<rl.blocks, rl.threads, 0, s>>>(xK, accK, gK, dotK, f32, p, g, vg);
+    count_launches(1);
+}
+
+// gz += (1 - f) (v_g Q_x + s_k V_k Q_g)  (= (1 - f) u (g_y Q_x + x_k Q_g)), and, when vg_next is
+// given, the next step's v_g = u g_y(k-1) = s_k (G_k - s_k <x_k, g_k> V_k) with
+// <x_k, g_k> = s_k * dsum (dsum = sum V_k B from the g-pass).
+__global__ void adjoint_combine_state_kernel(const float* f, const float* vg, const float* qx, const float* Vk,
+                                             const float* qg, const float* Gk, const double* acc_k,
+                                             const double* dsum, Geom g, float* gz, float* vg_next) {
+    const float sk = inv_norm_from(acc_k, nullptr);
+    const float dot = sk * (float)*dsum;
+    for_each_voxel(g, [&](int64_t, int64_t j) {
+        const float v = Vk[j];
+        gz[j] += (1.f - f[j]) * (vg[j] * qx[j] + sk * v * qg[j]);
+        if (vg_next) vg_next[j] = sk * (Gk[j] - sk * dot * v);
+    });
+}
+
+void launch_adjoint_combine_state(const float* f32, const float* vg, const float* qx, const float* Vk,
+                                  const float* qg, const float* Gk, const double* acc_k, const double* dsum, Geom g,
+                                  float* gz, float* vg_next, cudaStream_t s) {
+    const RowLaunch rl = row_launch(g, num_sms(), 8);
+    adjoint_combine_state_kernel<<<rl.blocks, rl.threads, 0, s>>>(f32, vg, qx, Vk, qg, Gk, acc_k, dsum, g, gz,
+                                                                   vg_next);
+    count_launches(1);
+}
+
+// V = u x~ for a checkpoint (internal layout), the start of a recomputed segment.
+void launch_state_internal(const float* x, const float* f32, float p, Geom g, float* v, cudaStream_t s) {
     const RowLaunch rl = row_launch(g, num_sms());
     state_internal_kernel<<<rl.blocks, rl.threads, 0, s>>>(x, f32, p, g, v);
     count_launches(1);
-    return launch_filter_fast(v, 3, y, nullptr, f32, g, tp, inv_alpha, p, acc_in, flags, s);
 }
 
 // g_K from the caller's layout into the internal layout, and <x_K, g_K>.

@@ -135,18 +135,20 @@ struct Params {
     int* flags;
     void* out;        // next state (internal pitch) or x~ (caller layout)
     const void* f;    // f in global memory (internal pitch), read by the epilogue
-    const float* s;   // separate unary map S_m (float32, internal pitch; SEP kernels only)
-    void* out2;       // second output of the adjoint filtering (MODE 2)
+    const float* s;   // separate unary map S_m (SEP kernels), or the state V_k (MODE 5); float32,
+                      // internal pitch
+    void* out2;       // second output: the record x~ (MODE 4) or Q (MODE 5)
 };
 
 // SEP: the unary term u = s^p comes from a separate map S_m (Eq. 9 with its own channels)
-// instead of from f.  MODE 0 is the power-iteration step.  MODEs 1 and 2 serve the adjoint
-// (kernels_bwd.cu): with c_0, c_1, c_2 the three filtered signals of the input (G*(u z),
-// G*(f^2 u z), G*(f u z) for v = u z), MODE 1 stores Q = a1 c_0 - p c_1 + a3 c_2 with
-// a1 = p (1/alpha - f^2) - 2 f^2, a3 = 2 (p + 1) f (the f-derivative weights of the step), and
-// MODE 2 stores A z = u B (B the Eq. 7 bracket) and Q, MODE 3 only A z; all scaled by s, in the
-// internal layout.  MODE 4 is the power-iteration step that also records x~ (internal layout,
-// out2) for the adjoint.
+// instead of from f.  MODE 0 is the power-iteration step; MODE 4 is the same step that also
+// records x~ (internal layout, out2) for the adjoint.  MODEs 1 and 5 serve the adjoint
+// (kernels_bwd.cu): with c_0, c_1, c_2 the three filtered signals of the input v (G*v,
+// G*(f^2 v), G*(f v)), Q = a1 c_0 - p c_1 + a3 c_2 with a1 = p (1/alpha - f^2) - 2 f^2,
+// a3 = 2 (p + 1) f (the f-derivative weights of the step).  MODE 1 stores s Q.  MODE 5 stores
+// G = u^2 B (B the Eq. 7 bracket, so G = u A z for v = u z) and Q, and adds sum V_k B over its
+// voxels to acc_out, with V_k = u x~_k read from P.s (so that <x_k, A z> = s_k sum V_k B needs
+// no division by u).  All in the internal layout.
 template <int RT, int RH, int RW, typename TS, typename TVO, bool OUT_X, bool SEP, int MODE>
 __global__ void __launch_bounds__(NTHR, SFSEG_FAST_MINB)
 iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtensorMap mf, Params P) {
@@ -235,11 +237,11 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
         // behind the two spatial passes.  Outside the volume f is taken as 0, so those
         // positions give x~ = 0 and add nothing to the norm (row padding is not relied on).
         float2 fo[4];
-        float2 so[SEP ? 4 : 1];
+        float2 so[(SEP || MODE == 5) ? 4 : 1];
 #pragma unroll
         for (int m = 0; m < 4; ++m) fo[m] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int m = 0; m < (SEP ? 4 : 1); ++m) so[m] = make_float2(0.f, 0.f);
+        for (int m = 0; m < ((SEP || MODE == 5) ? 4 : 1); ++m) so[m] = make_float2(0.f, 0.f);
         if (to >= t0 && h < g.H && wr < TH) {
             const TS* fg = reinterpret_cast<const TS*>(P.f) + ((int64_t)to * g.H + h) * g.pitch + wbase;
 #pragma unroll
@@ -247,7 +249,7 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
                 if (wbase + 2 * m + 1 < g.W) fo[m] = ld_pair(fg + 2 * m);
                 else if (wbase + 2 * m < g.W) fo[m].x = ldf(fg + 2 * m);
             }
-            if constexpr (SEP) {
+            if constexpr (SEP || MODE == 5) {
                 const float* sg = P.s + ((int64_t)to * g.H + h) * g.pitch + wbase;
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
@@ -332,7 +334,7 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
         // ---------------- Eq. 7 combination for frame to = tt - RT
         if (to >= t0 && wr < TH) {
             float2 outv[4];
-            float2 outq[(MODE == 2 || MODE == 4) ? 4 : 1];
+            float2 outq[(MODE == 4 || MODE == 5) ? 4 : 1];
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 const float2 fv = fo[m];
@@ -346,10 +348,6 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
                     part = fma2(xt, xt, part);
                     outv[m] = OUT_X ? xt : mul2(u, xt);
                     if constexpr (MODE == 4) outq[m] = xt;
-                } else if constexpr (MODE == 3) {
-                    float2 B = fma2(e, y[0][m], make_float2(-y[1][m].x, -y[1][m].y));
-                    B = fma2(mul2(f2(2.f), fv), y[2][m], B);
-                    outv[m] = mul2(mul2(s2, u), B);
                 } else {
                     const float2 a1 = fma2(f2(P.p), e, mul2(f2(-2.f), mul2(fv, fv)));
                     const float2 a3 = mul2(f2(2.f * (P.p + 1.f)), fv);
@@ -360,8 +358,9 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
                     } else {
                         float2 B = fma2(e, y[0][m], make_float2(-y[1][m].x, -y[1][m].y));
                         B = fma2(mul2(f2(2.f), fv), y[2][m], B);
-                        outv[m] = mul2(mul2(s2, u), B);
-                        outq[MODE == 2 ? m : 0] = Q;
+                        outv[m] = mul2(mul2(u, u), B);
+                        part = fma2(so[MODE == 5 ? m : 0], B, part);
+                        outq[MODE == 5 ? m : 0] = Q;
                     }
                 }
             }
@@ -378,17 +377,17 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
             if constexpr (MODE != 0 && MODE != 4) {
                 if (h < g.H) {
                     float* o = reinterpret_cast<float*>(P.out) + ((int64_t)to * g.H + h) * g.pitch + wbase;
-                    float* o2 = MODE == 2 ? reinterpret_cast<float*>(P.out2) + ((int64_t)to * g.H + h) * g.pitch + wbase
+                    float* o2 = MODE == 5 ? reinterpret_cast<float*>(P.out2) + ((int64_t)to * g.H + h) * g.pitch + wbase
                                           : nullptr;
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
                         if (wbase + 2 * m < g.W) {
                             o[2 * m] = outv[m].x;
-                            if (MODE == 2) o2[2 * m] = outq[MODE == 2 ? m : 0].x;
+                            if (MODE == 5) o2[2 * m] = outq[MODE == 5 ? m : 0].x;
                         }
                         if (wbase + 2 * m + 1 < g.W) {
                             o[2 * m + 1] = outv[m].y;
-                            if (MODE == 2) o2[2 * m + 1] = outq[MODE == 2 ? m : 0].y;
+                            if (MODE == 5) o2[2 * m + 1] = outq[MODE == 5 ? m : 0].y;
                         }
                     }
                 }
@@ -559,16 +558,20 @@ static bool dispatch_ckpt(const float* vin, void* out, bool out_x, const float* 
                                                              ckpt);
 }
 
-// The adjoint's filtering passes (MODE 1: Q; MODE 2: A z and Q; MODE 3: A z), float32 only.
+// The adjoint's Q-pass (MODE 1), float32 only.
 template <int RT, int RH, int RW>
 static bool dispatch_filter(const float* vin, int mode, float* out, float* out2, const float* f, const Geom& g,
                             const Taps& tp, float ia, float p, const double* ai, int* fl, cudaStream_t s) {
-    if (mode == 1)
-        return launch_t<RT, RH, RW, float, float, false, false, 1>(vin, out, f, g, tp, ia, p, ai, nullptr, fl, s);
-    if (mode == 3)
-        return launch_t<RT, RH, RW, float, float, false, false, 3>(vin, out, f, g, tp, ia, p, ai, nullptr, fl, s);
-    return launch_t<RT, RH, RW, float, float, false, false, 2>(vin, out, f, g, tp, ia, p, ai, nullptr, fl, s, nullptr,
-                                                             out2);
+    (void)out2;
+    if (mode != 1) return false;
+    return launch_t<RT, RH, RW, float, float, false, false, 1>(vin, out, f, g, tp, ia, p, ai, nullptr, fl, s);
+}
+
+// The adjoint's g-pass in state form (MODE 5), float32 only.
+template <int RT, int RH, int RW>
+static bool dispatch_gpass(const float* vg, float* G, float* Qg, const float* Vk, const float* f, const Geom& g,
+                           const Taps& tp, float ia, float p, double* dot, int* fl, cudaStream_t s) {
+    return launch_t<RT, RH, RW, float, float, false, false, 5>(vg, G, f, g, tp, ia, p, nullptr, dot, fl, s, Vk, Qg);
 }
 
 }  // namespace fast
@@ -613,6 +616,16 @@ bool launch_filter_fast(const float* vin, int mode, float* out, float* out2, con
 #define SFSEG_GO(A, B, C)                                                                                     \
     if (tp.rt == A && tp.rh == B && tp.rw == C)                                                               \
         return fast::dispatch_filter<A, B, C>(vin, mode, out, out2, f, g, tp, inv_alpha, p, acc_in, flags, s);
+    SFSEG_FAST_RADII(SFSEG_GO)
+#undef SFSEG_GO
+    return false;
+}
+
+bool launch_adjoint_gpass_fast(const float* vg, float* G, float* Qg, const float* Vk, const float* f, const Geom& g,
+                               const Taps& tp, float inv_alpha, float p, double* dot, int* flags, cudaStream_t s) {
+#define SFSEG_GO(A, B, C)                                                                                  \
+    if (tp.rt == A && tp.rh == B && tp.rw == C)                                                            \
+        return fast::dispatch_gpass<A, B, C>(vg, G, Qg, Vk, f, g, tp, inv_alpha, p, dot, flags, s);
     SFSEG_FAST_RADII(SFSEG_GO)
 #undef SFSEG_GO
     return false;

@@ -49,12 +49,19 @@ bool launch_iterate_fast_ckpt(const float* vin, void* out, bool out_x, const flo
                               float inv_alpha, float p, const double* acc_in, double* acc_out, float* ckpt, int* flags,
                               cudaStream_t s);
 
-// The adjoint's filtering passes on the TMA kernel (kernels_fast.cu), float32, internal layout:
-// for v = u z (scaled by s = 1/sqrt(*acc_in), or 1), mode 1 writes Q = s (a1 c0 - p c1 + a3 c2)
-// to out; mode 2 writes A z (scaled) to out and Q to out2; mode 3 writes only A z.  Returns
-// false (nothing launched) for a radius without a compiled kernel.
+// The adjoint's Q-pass on the TMA kernel (kernels_fast.cu, mode 1), float32, internal layout:
+// for the signals c0, c1, c2 of v (G*v, G*(f^2 v), G*(f v)), writes Q = s (a1 c0 - p c1 + a3 c2)
+// to out, s = 1/sqrt(*acc_in) (or 1).  Returns false (nothing launched) for another mode or a
+// radius without a compiled kernel.
 bool launch_filter_fast(const float* vin, int mode, float* out, float* out2, const float* f, const Geom& g,
                         const Taps& tp, float inv_alpha, float p, const double* acc_in, int* flags, cudaStream_t s);
+
+// The adjoint's g-pass in state form (kernels_fast.cu, mode 5): for v_g = u g_y, writes
+// G = u A g_y = u^2 B to G and Q (unscaled) to Qg, and adds sum V_k B to *dot (V_k = u x~_k,
+// internal layout; <x_k, A g_y> = dot / ||x~_k||).  Returns false for a radius without a
+// compiled kernel.
+bool launch_adjoint_gpass_fast(const float* vg, float* G, float* Qg, const float* Vk, const float* f, const Geom& g,
+                               const Taps& tp, float inv_alpha, float p, double* dot, int* flags, cudaStream_t s);
 
 // y = s * A x in the plain (x-space) form: x with pitch x_pitch, y with pitch y_pitch, FP32
 // features; s = 1/sqrt(*acc_in) (or 1 if acc_in is null); acc_out += ||y||^2 (nullable).
@@ -110,17 +117,16 @@ void launch_adjoint_step(const float* xk, const double* acc_k, const float* xn, 
                          const float* gn, const double* dot_n, float* gk_out, double* dot_k,
                          float* gz, const float* f32, Geom g, const Taps& tp, float inv_alpha,
                          float p, cudaStream_t s);
-// The same step through the TMA kernel's filtering passes (false, with nothing or only the
-// preparation launched, for a radius without a TMA kernel: then run launch_adjoint_step).
-// work: four internal-layout float volumes.
-bool launch_adjoint_step_fast(const float* xk, const double* acc_k, const float* xn, const double* acc_n,
-                              const float* gn, const double* dot_n, float* gk_out, double* dot_k, float* gz,
-                              const float* f32, Geom g, const Taps& tp, float inv_alpha, float p, float* const work[4],
-                              int* flags, cudaStream_t s);
-// y = s A x for x, y in the internal layout (s = 1/sqrt(*acc_in)) through the TMA kernel, v a
-// scratch volume; false (only the conversion launched) for a radius without a TMA kernel.
-bool launch_apply_internal_fast(const float* x, float* y, float* v, const float* f32, Geom g, const Taps& tp,
-                                float inv_alpha, float p, const double* acc_in, int* flags, cudaStream_t s);
+// The reverse step in the stencil's state form (kernels_bwd.cu; V_k = u x~_k, G_k = u g_k,
+// v_g = u g_y, all internal layout): the first step's v_g from x~_K, g_K and <x_K, g_K>; the
+// element-wise pass after the g-pass (gz += (1 - f)(v_g Q_x + s_k V_k Q_g), and the next v_g
+// when vg_next is not null); and V = u x~ for a recomputed segment's checkpoint.
+void launch_adjoint_first(const float* xK, const double* accK, const float* gK, const double* dotK,
+                          const float* f32, float p, Geom g, float* vg, cudaStream_t s);
+void launch_adjoint_combine_state(const float* f32, const float* vg, const float* qx, const float* Vk,
+                                  const float* qg, const float* Gk, const double* acc_k, const double* dsum, Geom g,
+                                  float* gz, float* vg_next, cudaStream_t s);
+void launch_state_internal(const float* x, const float* f32, float p, Geom g, float* v, cudaStream_t s);
 void launch_weight_grad(const void* feat, int feat_dtype, int C, Geom g, const float* gz,
                         double* acc_c_plus_1, cudaStream_t s);
 void launch_soft_iou(const float* x, const float* tgt, int64_t n, float* grad, double* acc,
