@@ -105,6 +105,22 @@ __device__ __forceinline__ float2 ld_pair(const __nv_bfloat16* p) {
     return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
 }
 
+// Four pairs of float32 values to columns wbase .. wbase + 7 of an internal-layout row (pitch a
+// multiple of 32, wbase of 8): two 16-byte stores when all eight columns are below W, else one
+// value at a time.
+__device__ __forceinline__ void st_pairs(float* o, const float2 p[4], int wbase, int W) {
+    if (wbase + 8 <= W) {
+        reinterpret_cast<float4*>(o)[0] = make_float4(p[0].x, p[0].y, p[1].x, p[1].y);
+        reinterpret_cast<float4*>(o)[1] = make_float4(p[2].x, p[2].y, p[3].x, p[3].y);
+    } else {
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            if (wbase + 2 * m < W) o[2 * m] = p[m].x;
+            if (wbase + 2 * m + 1 < W) o[2 * m + 1] = p[m].y;
+        }
+    }
+}
+
 template <int RT, int RH, int RW, typename TS, typename TVO, bool OUT_X>
 struct Cfg {
     static constexpr int BH = TH + 2 * RH;                // TMA box height
@@ -367,28 +383,16 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
             if constexpr (MODE == 4) {
                 if (h < g.H) {
                     float* o2 = reinterpret_cast<float*>(P.out2) + ((int64_t)to * g.H + h) * g.pitch + wbase;
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        if (wbase + 2 * m < g.W) o2[2 * m] = outq[m].x;
-                        if (wbase + 2 * m + 1 < g.W) o2[2 * m + 1] = outq[m].y;
-                    }
+                    st_pairs(o2, outq, wbase, g.W);
                 }
             }
             if constexpr (MODE != 0 && MODE != 4) {
                 if (h < g.H) {
                     float* o = reinterpret_cast<float*>(P.out) + ((int64_t)to * g.H + h) * g.pitch + wbase;
-                    float* o2 = MODE == 5 ? reinterpret_cast<float*>(P.out2) + ((int64_t)to * g.H + h) * g.pitch + wbase
-                                          : nullptr;
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        if (wbase + 2 * m < g.W) {
-                            o[2 * m] = outv[m].x;
-                            if (MODE == 5) o2[2 * m] = outq[MODE == 5 ? m : 0].x;
-                        }
-                        if (wbase + 2 * m + 1 < g.W) {
-                            o[2 * m + 1] = outv[m].y;
-                            if (MODE == 5) o2[2 * m + 1] = outq[MODE == 5 ? m : 0].y;
-                        }
+                    st_pairs(o, outv, wbase, g.W);
+                    if constexpr (MODE == 5) {
+                        float* o2 = reinterpret_cast<float*>(P.out2) + ((int64_t)to * g.H + h) * g.pitch + wbase;
+                        st_pairs(o2, outq, wbase, g.W);
                     }
                 }
             } else
