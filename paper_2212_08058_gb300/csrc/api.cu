@@ -106,8 +106,9 @@ struct sfseg_handle {
     // adjoint workspace
     float* gbuf[2] = {nullptr, nullptr};
     float* gz = nullptr;
-    float* adjw[4] = {nullptr, nullptr, nullptr, nullptr};   // TMA-path adjoint workspace
+    float* adjw[3] = {nullptr, nullptr, nullptr};   // TMA-path adjoint workspace (Q_g, v_g, v_g)
     std::vector<float*> seg;
+    std::vector<float*> qxs;   // TMA path: Q_x of each step of the segment being reversed
     double* dots = nullptr;
     int dots_cap = 0;
     // optional CUDA-event timing of the iteration kernels
@@ -345,6 +346,7 @@ int sfseg_destroy(sfseg_handle* h) {
     cudaFree(h->gbuf[1]);
     cudaFree(h->gz);
     for (float* p : h->seg) cudaFree(p);
+    for (float* p : h->qxs) cudaFree(p);
     cudaFree(h->dots);
     for (sfseg_handle* c : h->lvl) sfseg_destroy(c);
     for (float* p : h->lvl_f) cudaFree(p);
@@ -632,6 +634,11 @@ int sfseg_backward(sfseg_handle* h, const sfseg_neighborhood* nb, const float* g
         SFSEG_CUDA(dalloc(&q, (size_t)h->NP));
         h->seg.push_back(q);
     }
+    while (fast_adj && (int)h->qxs.size() < c) {
+        float* q = nullptr;
+        SFSEG_CUDA(dalloc(&q, (size_t)h->NP));
+        h->qxs.push_back(q);
+    }
     if (int rc = ensure_acc(&h->dots, &h->dots_cap, K + 2)) return rc;
     // The launch sequence of the reverse pass (capturable: no allocation, no host synchronisation).
     auto enqueue = [&](cudaStream_t st) -> int {
@@ -643,30 +650,34 @@ int sfseg_backward(sfseg_handle* h, const sfseg_neighborhood* nb, const float* g
         SFSEG_LAUNCHED();
         const int nseg = (K + c - 1) / c;
         if (fast_adj) {
-            // State form on the TMA kernel: V_k in seg[k - k0], Q_x in adjw[0], Q_g in adjw[1], v_g
-            // alternating between adjw[2] and adjw[3], G_k in gbuf[1]; dots[k] = sum V_k B (k < K).
-            float* vg_cur = h->adjw[2];
-            float* vg_nxt = h->adjw[3];
+            // State form on the TMA kernel: V_k in seg[k - k0], Q_x(k) in qxs[k - k0], Q_g in adjw[0],
+            // v_g alternating between adjw[1] and adjw[2], G_k in gbuf[1]; dots[k] = sum V_k B (k < K).
+            float* vg_cur = h->adjw[1];
+            float* vg_nxt = h->adjw[2];
             launch_adjoint_first(xK, h->rec_acc + K, h->gbuf[0], h->dots + K, h->f32, p, h->g, vg_cur, st);
             SFSEG_LAUNCHED();
             for (int sgi = nseg - 1; sgi >= 0; --sgi) {
-                const int k0 = sgi * c, k1 = (k0 + c < K) ? k0 + c : K;
+                const int k0 = sgi * c, k1 = (k0 + c < K) ? k0 + c : K, n = k1 - k0;
                 launch_state_internal(h->ckpt[sgi], h->f32, p, h->g, h->seg[0], st);
                 SFSEG_LAUNCHED();
-                for (int i = 1; i < k1 - k0; ++i) {   // V_{k0+i}: the plain step from the recorded norm
-                    if (!launch_iterate_fast(h->seg[i - 1], kF32, h->seg[i], kF32, false, h->f32, h->g, tp, inv_alpha,
-                                             p, h->rec_acc + k0 + i - 1, nullptr, h->flags, st))
+                // V_{k0+i} by the plain step from the recorded norm, with Q_x(k0+i-1) of the same
+                // filtering; the segment's last Q_x by the Q-pass alone
+                for (int i = 1; i < n; ++i) {
+                    if (!launch_step_q_fast(h->seg[i - 1], h->seg[i], h->qxs[i - 1], h->f32, h->g, tp, inv_alpha, p,
+                                            h->rec_acc + k0 + i - 1, h->flags, st))
                         return fail(SFSEG_ERR_CUDA, "the TMA stencil could not be launched");
                     SFSEG_LAUNCHED();
                 }
+                if (!launch_filter_fast(h->seg[n - 1], 1, h->qxs[n - 1], nullptr, h->f32, h->g, tp, inv_alpha, p,
+                                        h->rec_acc + k1 - 1, h->flags, st))
+                    return fail(SFSEG_ERR_CUDA, "the TMA stencil could not be launched");
+                SFSEG_LAUNCHED();
                 for (int k = k1 - 1; k >= k0; --k) {
                     const float* Vk = h->seg[k - k0];
-                    if (!launch_filter_fast(Vk, 1, h->adjw[0], nullptr, h->f32, h->g, tp, inv_alpha, p,
-                                            h->rec_acc + k, h->flags, st) ||
-                        !launch_adjoint_gpass_fast(vg_cur, h->gbuf[1], h->adjw[1], Vk, h->f32, h->g, tp, inv_alpha, p,
+                    if (!launch_adjoint_gpass_fast(vg_cur, h->gbuf[1], h->adjw[0], Vk, h->f32, h->g, tp, inv_alpha, p,
                                                    h->dots + k, h->flags, st))
                         return fail(SFSEG_ERR_CUDA, "the TMA stencil could not be launched");
-                    launch_adjoint_combine_state(h->f32, vg_cur, h->adjw[0], Vk, h->adjw[1], h->gbuf[1],
+                    launch_adjoint_combine_state(h->f32, vg_cur, h->qxs[k - k0], Vk, h->adjw[0], h->gbuf[1],
                                                  h->rec_acc + k, h->dots + k, h->g, h->gz, k > 0 ? vg_nxt : nullptr, st);
                     SFSEG_LAUNCHED();
                     std::swap(vg_cur, vg_nxt);

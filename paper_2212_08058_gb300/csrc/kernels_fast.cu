@@ -153,7 +153,7 @@ struct Params {
     const void* f;    // f in global memory (internal pitch), read by the epilogue
     const float* s;   // separate unary map S_m (SEP kernels), or the state V_k (MODE 5); float32,
                       // internal pitch
-    void* out2;       // second output: the record x~ (MODE 4) or Q (MODE 5)
+    void* out2;       // second output: the record x~ (MODE 4) or Q (MODEs 5 and 6)
 };
 
 // SEP: the unary term u = s^p comes from a separate map S_m (Eq. 9 with its own channels)
@@ -164,7 +164,8 @@ struct Params {
 // a3 = 2 (p + 1) f (the f-derivative weights of the step).  MODE 1 stores s Q.  MODE 5 stores
 // G = u^2 B (B the Eq. 7 bracket, so G = u A z for v = u z) and Q, and adds sum V_k B over its
 // voxels to acc_out, with V_k = u x~_k read from P.s (so that <x_k, A z> = s_k sum V_k B needs
-// no division by u).  All in the internal layout.
+// no division by u).  MODE 6 is the step (MODE 0, the state to out) that also stores s Q to out2:
+// the adjoint's recomputation and Q-pass share the filtering of V_k.  All in the internal layout.
 template <int RT, int RH, int RW, typename TS, typename TVO, bool OUT_X, bool SEP, int MODE>
 __global__ void __launch_bounds__(NTHR, SFSEG_FAST_MINB)
 iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtensorMap mf, Params P) {
@@ -350,20 +351,26 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
         // ---------------- Eq. 7 combination for frame to = tt - RT
         if (to >= t0 && wr < TH) {
             float2 outv[4];
-            float2 outq[(MODE == 4 || MODE == 5) ? 4 : 1];
+            float2 outq[(MODE >= 4) ? 4 : 1];
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 const float2 fv = fo[m];
                 const float2 sv = SEP ? so[SEP ? m : 0] : fv;
                 const float2 u = make_float2(unary_pow_fast(sv.x, P.p), unary_pow_fast(sv.y, P.p));
                 const float2 e = fma2(make_float2(-fv.x, -fv.y), fv, f2(P.inv_alpha));   // 1/alpha - f^2
-                if constexpr (MODE == 0 || MODE == 4) {
+                if constexpr (MODE == 0 || MODE == 4 || MODE == 6) {
                     float2 B = fma2(e, y[0][m], make_float2(-y[1][m].x, -y[1][m].y));
                     B = fma2(mul2(f2(2.f), fv), y[2][m], B);
                     const float2 xt = mul2(mul2(s2, u), B);
                     part = fma2(xt, xt, part);
                     outv[m] = OUT_X ? xt : mul2(u, xt);
                     if constexpr (MODE == 4) outq[m] = xt;
+                    if constexpr (MODE == 6) {
+                        const float2 a1 = fma2(f2(P.p), e, mul2(f2(-2.f), mul2(fv, fv)));
+                        const float2 a3 = mul2(f2(2.f * (P.p + 1.f)), fv);
+                        const float2 Q = fma2(a1, y[0][m], mul2(f2(-P.p), y[1][m]));
+                        outq[MODE == 6 ? m : 0] = mul2(s2, fma2(a3, y[2][m], Q));
+                    }
                 } else {
                     const float2 a1 = fma2(f2(P.p), e, mul2(f2(-2.f), mul2(fv, fv)));
                     const float2 a3 = mul2(f2(2.f * (P.p + 1.f)), fv);
@@ -380,13 +387,13 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
                     }
                 }
             }
-            if constexpr (MODE == 4) {
+            if constexpr (MODE == 4 || MODE == 6) {
                 if (h < g.H) {
                     float* o2 = reinterpret_cast<float*>(P.out2) + ((int64_t)to * g.H + h) * g.pitch + wbase;
                     st_pairs(o2, outq, wbase, g.W);
                 }
             }
-            if constexpr (MODE != 0 && MODE != 4) {
+            if constexpr (MODE == 1 || MODE == 5) {
                 if (h < g.H) {
                     float* o = reinterpret_cast<float*>(P.out) + ((int64_t)to * g.H + h) * g.pitch + wbase;
                     st_pairs(o, outv, wbase, g.W);
@@ -571,6 +578,14 @@ static bool dispatch_filter(const float* vin, int mode, float* out, float* out2,
     return launch_t<RT, RH, RW, float, float, false, false, 1>(vin, out, f, g, tp, ia, p, ai, nullptr, fl, s);
 }
 
+// The adjoint's recomputing step with its Q-pass (MODE 6), float32 only.
+template <int RT, int RH, int RW>
+static bool dispatch_step_q(const float* vin, float* vout, float* Q, const float* f, const Geom& g, const Taps& tp,
+                            float ia, float p, const double* ai, int* fl, cudaStream_t s) {
+    return launch_t<RT, RH, RW, float, float, false, false, 6>(vin, vout, f, g, tp, ia, p, ai, nullptr, fl, s, nullptr,
+                                                             Q);
+}
+
 // The adjoint's g-pass in state form (MODE 5), float32 only.
 template <int RT, int RH, int RW>
 static bool dispatch_gpass(const float* vg, float* G, float* Qg, const float* Vk, const float* f, const Geom& g,
@@ -630,6 +645,16 @@ bool launch_adjoint_gpass_fast(const float* vg, float* G, float* Qg, const float
 #define SFSEG_GO(A, B, C)                                                                                  \
     if (tp.rt == A && tp.rh == B && tp.rw == C)                                                            \
         return fast::dispatch_gpass<A, B, C>(vg, G, Qg, Vk, f, g, tp, inv_alpha, p, dot, flags, s);
+    SFSEG_FAST_RADII(SFSEG_GO)
+#undef SFSEG_GO
+    return false;
+}
+
+bool launch_step_q_fast(const float* vin, float* vout, float* Q, const float* f, const Geom& g, const Taps& tp,
+                        float inv_alpha, float p, const double* acc_in, int* flags, cudaStream_t s) {
+#define SFSEG_GO(A, B, C)                                                                                  \
+    if (tp.rt == A && tp.rh == B && tp.rw == C)                                                            \
+        return fast::dispatch_step_q<A, B, C>(vin, vout, Q, f, g, tp, inv_alpha, p, acc_in, flags, s);
     SFSEG_FAST_RADII(SFSEG_GO)
 #undef SFSEG_GO
     return false;

@@ -56,6 +56,13 @@ bool launch_iterate_fast_ckpt(const float* vin, void* out, bool out_x, const flo
 bool launch_filter_fast(const float* vin, int mode, float* out, float* out2, const float* f, const Geom& g,
                         const Taps& tp, float inv_alpha, float p, const double* acc_in, int* flags, cudaStream_t s);
 
+// The adjoint's recomputing step with its Q-pass (kernels_fast.cu, mode 6): from the state V_k
+// (internal layout, s = 1/sqrt(*acc_in)) writes the next state to vout exactly as the plain step
+// does, and Q = s (a1 c0 - p c1 + a3 c2) of the same filtered signals to Q.  Returns false for a
+// radius without a compiled kernel.
+bool launch_step_q_fast(const float* vin, float* vout, float* Q, const float* f, const Geom& g, const Taps& tp,
+                        float inv_alpha, float p, const double* acc_in, int* flags, cudaStream_t s);
+
 // The adjoint's g-pass in state form (kernels_fast.cu, mode 5): for v_g = u g_y, writes
 // G = u A g_y = u^2 B to G and Q (unscaled) to Qg, and adds sum V_k B to *dot (V_k = u x~_k,
 // internal layout; <x_k, A g_y> = dot / ||x~_k||).  Returns false for a radius without a

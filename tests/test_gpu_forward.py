@@ -252,6 +252,67 @@ def test_kronecker_eigenpair_full_size():
     assert res < 1e-5
 
 
+def test_invariants_480p():
+    """The invariants that hold on every run, on the benchmark's workload (three crossing blobs,
+    64 x 480 x 854, radius (2,7,7), 50 iterations from the uniform start; alpha = 1 and f in
+    [0, 1], so M >= 0): x >= 0; the norms nu_k = ||A x_{k-1}|| do not decrease (for symmetric A,
+    ||A^k x0|| is log-convex in k); the Eq. 3 quotient is at most the largest row sum max(A 1);
+    and a slab of rt frames with f = 0 (u = 0) decouples the frames before it from the frames
+    after it: A maps a vector supported before the slab to one that is exactly 0 after it."""
+    sf = _sf()
+    T, H, W = 64, 480, 854
+    r = (2, 7, 7)
+    V = synth.crossing_blobs(T, H, W, seed=2000)
+    with sf.PowerIteration(1, T, H, W) as h:
+        feats = torch.from_numpy(np.ascontiguousarray(V)).cuda()
+        x, nu = h.power_iterate(feats, radius=r, iters=50, return_norms=True)
+        assert float(x.min()) >= 0.0
+        nu = np.asarray(nu)
+        assert np.all(nu[1:] >= nu[:-1] * (1 - 1e-6)), np.min(nu[1:] / nu[:-1])
+        rho, _ = h.rayleigh(x, r)
+        rowsum = float(h.apply(torch.ones((T, H, W), device="cuda"), r).max())
+        assert rho <= rowsum * (1 + 1e-6)
+        # decoupling: zero f on frames [30, 30 + rt)
+        Vz = V.copy()
+        Vz[:, 30:30 + r[0]] = 0.0
+        h.set_features(torch.from_numpy(np.ascontiguousarray(Vz)).cuda())
+        y = torch.zeros((T, H, W), device="cuda")
+        y[:30] = torch.rand((30, H, W), device="cuda")
+        Ay = h.apply(y, r)
+        assert float(Ay[30:].abs().max()) == 0.0
+        assert float(Ay[:30].abs().max()) > 0.0
+
+
+def test_kronecker_eigenpair_1080p():
+    """The same closed form at the warm-start volume's shape, 120 x 1080 x 1920 (2.49e8 voxels,
+    the outer product built on the device): A v = lambda v, the Eq. 3 quotient and residual."""
+    sf = _sf()
+    T, H, W = 120, 1080, 1920
+    r = (2, 7, 7)
+    sig = sf.default_sigma(r)
+    fval, p = 0.35, 0.1
+
+    def band(n, ra, sa):
+        d = np.arange(n)[:, None] - np.arange(n)[None, :]
+        return np.where(np.abs(d) <= ra, np.exp(-d * d / (2 * sa * sa)), 0.0)
+
+    vals, vecs = [], []
+    for n, ra, sa in zip((T, H, W), r, sig):
+        e, Vv = np.linalg.eigh(band(n, ra, sa))
+        vals.append(e[-1])
+        vecs.append(torch.from_numpy(Vv[:, -1] * np.sign(Vv[:, -1].sum())).float().cuda())
+    lam = fval ** (2 * p) * vals[0] * vals[1] * vals[2]
+    v = torch.einsum("a,b,c->abc", *vecs).contiguous()
+    with sf.PowerIteration(1, T, H, W, p=p) as h:
+        h.set_features(torch.full((1, T, H, W), fval, device="cuda"))
+        Av = h.apply(v, r)
+        rho, res = h.rayleigh(v, r)
+    err = float((Av - lam * v).abs().max())
+    assert err <= 2e-6 * lam * float(v.abs().max())
+    assert abs(rho - lam) <= 1e-5 * lam
+    assert res < 1e-5
+
+
 def test_full_size_sfsegpp_bf16_parity():
     """SFSeg++ at the 480p shape: C = 8 channels of 64 x 480 x 854 in bf16 (multichannel recipe),
     radius (2,7,7), every iteration in bf16 storage, in the launch configuration the benchmark's
