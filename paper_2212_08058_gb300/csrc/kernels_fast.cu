@@ -405,11 +405,18 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
             } else
             if (h < g.H) {
                 if (OUT_X) {
+                    // caller layout: rows of W values, 8-byte aligned when W is even (and the
+                    // caller's base is), then one 8-byte store per pair
                     float* o = reinterpret_cast<float*>(P.out) + ((int64_t)to * g.H + h) * g.W + wbase;
+                    if (wbase + 8 <= g.W && (reinterpret_cast<uintptr_t>(o) & 7) == 0) {
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        if (wbase + 2 * m < g.W) o[2 * m] = outv[m].x;
-                        if (wbase + 2 * m + 1 < g.W) o[2 * m + 1] = outv[m].y;
+                        for (int m = 0; m < 4; ++m) reinterpret_cast<float2*>(o)[m] = outv[m];
+                    } else {
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            if (wbase + 2 * m < g.W) o[2 * m] = outv[m].x;
+                            if (wbase + 2 * m + 1 < g.W) o[2 * m + 1] = outv[m].y;
+                        }
                     }
                 } else {
                     TVO* o = reinterpret_cast<TVO*>(P.out) + ((int64_t)to * g.H + h) * g.pitch + wbase;
