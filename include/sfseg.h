@@ -135,6 +135,34 @@ int sfseg_power_iterate(sfseg_handle* h, const void* features, int dtype, const 
 int sfseg_apply(sfseg_handle* h, const sfseg_neighborhood* nb, const float* x, float* y,
                 void* stream);
 
+/* The exact kernel (Eq. 1 instead of its first-order expansion Eq. 2), the diagnostic of the
+ * approximation (Sec. 4.3, the Fig. 4 comparison): y = (1/alpha) M x with
+ * M_ij = u_i u_j exp(-alpha (f_i - f_j)^2) G_ij on the same box, Gaussian and zero padding as
+ * sfseg_apply (the 1/alpha matches A = M/alpha of Eq. 7, so both operators have comparable
+ * eigenvalues; eigenvectors do not depend on it).  Computed without forming M, through the
+ * series exp(-alpha (f_i - f_j)^2) = e^{-alpha f_i^2} e^{-alpha f_j^2} sum_n (2 alpha f_i f_j)^n / n!,
+ * whose terms are separable: three terms per pass of the TMA stencil.  Shared maps only
+ * (UNSUPPORTED after sfseg_set_features_sf), the radii with a TMA kernel only (UNSUPPORTED
+ * otherwise), FP32 storage.
+ *   n_terms   the number of series terms, 1..120; 0 chooses the smallest count whose tail
+ *             bound x^(N+1)/(N+1)! e^x, x = 2 alpha max(f)^2, is below 2^-24 relative to the sum
+ *             (this reads max f: the call synchronises), or returns UNSUPPORTED when 120 terms
+ *             do not reach it.
+ *   x, y      device [T][H][W] float32 (may not alias).
+ * Errors: INVALID_ARG, SHAPE, STATE (no features), UNSUPPORTED, OOM, CUDA. */
+int sfseg_apply_exact(sfseg_handle* h, const sfseg_neighborhood* nb, int n_terms, const float* x,
+                      float* y, void* stream);
+
+/* Power iteration (Eq. 4 with the Eq. 8 normalisation) on the exact kernel's operator above:
+ * `iters` steps from x_inout (init SFSEG_INIT_USER) or from the uniform vector
+ * (SFSEG_INIT_UNIFORM); x_inout (device [T][H][W] float32) is overwritten with the unit-norm
+ * x_iters.  n_terms as for sfseg_apply_exact.  norms_out: host array of `iters` doubles or NULL
+ * (as for sfseg_power_iterate; synchronises when given).  Each step costs ceil(n_terms / 3)
+ * stencil passes.  Errors: those of sfseg_apply_exact, and with norms_out ZERO_NORM /
+ * NONFINITE. */
+int sfseg_power_iterate_exact(sfseg_handle* h, const sfseg_neighborhood* nb, int n_terms, int iters,
+                              int init, float* x_inout, double* norms_out, void* stream);
+
 /* Eq. 3: Rayleigh quotient rho = x'Ax / x'x and eigen-residual ||Ax - rho x|| / (rho ||x||)
  * of the FP32 operator (FP64 reductions).  x: device [T][H][W] float32.  rho, residual: host
  * doubles (either may be NULL).  Synchronises the stream.  Uses the handle's iterate buffer as

@@ -109,6 +109,7 @@ struct sfseg_handle {
     float* adjw[3] = {nullptr, nullptr, nullptr};   // TMA-path adjoint workspace (Q_g, v_g, v_g)
     std::vector<float*> seg;
     std::vector<float*> qxs;   // TMA path: Q_x of each step of the segment being reversed
+    float* exv = nullptr;      // the exact kernel's term input (internal layout)
     double* dots = nullptr;
     int dots_cap = 0;
     // optional CUDA-event timing of the iteration kernels
@@ -347,6 +348,7 @@ int sfseg_destroy(sfseg_handle* h) {
     cudaFree(h->gz);
     for (float* p : h->seg) cudaFree(p);
     for (float* p : h->qxs) cudaFree(p);
+    cudaFree(h->exv);
     cudaFree(h->dots);
     for (sfseg_handle* c : h->lvl) sfseg_destroy(c);
     for (float* p : h->lvl_f) cudaFree(p);
@@ -581,6 +583,128 @@ int sfseg_apply(sfseg_handle* h, const sfseg_neighborhood* nb, const float* x, f
     launch_apply_user(x, y, (float*)h->vbuf[1], h->f32, h->g, tp, (float)(1.0 / h->alpha), (float)h->p, h->flags,
                       (cudaStream_t)stream, h->sep ? h->s32 : nullptr);
     SFSEG_LAUNCHED();
+    return SFSEG_OK;
+}
+
+// ------------------------------------------------------------- the exact (Eq. 1) kernel
+namespace {
+constexpr int kExactMaxTerms = 120;   // 40 launches of three terms
+
+// The series length N + 1: n_terms if given, else the smallest N whose tail bound
+// x^(N+1)/(N+1)! e^x (x = 2 alpha max(f)^2, relative to the series' sum >= 1) is below 2^-24.
+int exact_terms(sfseg_handle* h, int n_terms, cudaStream_t s, int* terms_out) {
+    if (n_terms < 0 || n_terms > kExactMaxTerms)
+        return fail(SFSEG_ERR_INVALID_ARG, "n_terms must be in [0, 120] (0: chosen from alpha and max f)");
+    if (n_terms > 0) {
+        *terms_out = n_terms;
+        return SFSEG_OK;
+    }
+    unsigned* key = reinterpret_cast<unsigned*>(h->scratch + kScrMaxKey);
+    SFSEG_CUDA(cudaMemsetAsync(key, 0, sizeof(unsigned), s));
+    launch_max_key(h->f32, h->NP, key, s);
+    SFSEG_LAUNCHED();
+    unsigned k = 0;
+    SFSEG_CUDA(cudaMemcpyAsync(&k, key, sizeof(k), cudaMemcpyDeviceToHost, s));
+    SFSEG_CUDA(cudaStreamSynchronize(s));
+    uint32_t b = (k & 0x80000000u) ? (k & 0x7fffffffu) : ~k;
+    float fmax;
+    std::memcpy(&fmax, &b, sizeof(fmax));
+    const double x = 2.0 * h->alpha * (double)fmax * fmax;
+    double tail = x * std::exp(x);   // x^(N+1)/(N+1)! e^x for N = 0
+    for (int n = 1; n <= kExactMaxTerms; ++n) {
+        if (tail <= std::ldexp(1.0, -24)) {
+            *terms_out = n;
+            return SFSEG_OK;
+        }
+        tail *= x / (n + 1);
+    }
+    return fail(SFSEG_ERR_UNSUPPORTED, "alpha * max(f)^2 too large for the series form of the exact kernel");
+}
+
+// y = (1/alpha) M x~ s (s = 1/sqrt(*acc_in), or 1), internal layout; acc_out += ||y||^2.
+int exact_apply(sfseg_handle* h, const Taps& tp, int terms, const float* xt, const double* acc_in, float* y,
+                double* acc_out, cudaStream_t s) {
+    const double a = h->alpha;
+    std::vector<double> c((size_t)terms + 2, 0.0);
+    c[0] = 1.0;
+    for (int n = 1; n < terms; ++n) c[n] = c[n - 1] * 2.0 * a / n;
+    const int groups = (terms + 2) / 3;
+    for (int j = 0; j < groups; ++j) {
+        launch_exact_prep(xt, acc_in, h->f32, (float)a, (float)h->p, j, h->g, h->exv, h->flags, s);
+        SFSEG_LAUNCHED();
+        ExactTerm ex;
+        ex.j = j;
+        ex.last = j == groups - 1;
+        for (int i = 0; i < 3; ++i) ex.c[i] = 3 * j + i < terms ? (float)c[3 * j + i] : 0.f;
+        ex.alpha = (float)a;
+        if (!launch_exact_term_fast(h->exv, y, h->f32, h->g, tp, (float)(1.0 / a), (float)h->p, ex,
+                                    ex.last ? acc_out : nullptr, h->flags, s))
+            return fail(SFSEG_ERR_CUDA, "the TMA stencil could not be launched");
+        SFSEG_LAUNCHED();
+    }
+    return SFSEG_OK;
+}
+
+int exact_checks(sfseg_handle* h, const Taps& tp) {
+    if (!h->features_set) return fail(SFSEG_ERR_STATE, "no features set");
+    if (h->sep) return fail(SFSEG_ERR_UNSUPPORTED, "the exact kernel is for shared maps (S = F)");
+    if (!fast_iterate_supported(tp))
+        return fail(SFSEG_ERR_UNSUPPORTED, "the exact kernel runs on the radii with a TMA kernel only");
+    if (!h->exv) SFSEG_CUDA(dalloc(&h->exv, (size_t)h->NP));
+    return SFSEG_OK;
+}
+}  // namespace
+
+int sfseg_apply_exact(sfseg_handle* h, const sfseg_neighborhood* nb, int n_terms, const float* x, float* y,
+                      void* stream) {
+    if (int rc = check_handle(h)) return rc;
+    Taps tp;
+    if (int rc = make_taps(nb, &tp)) return rc;
+    if (!x || !y) return fail(SFSEG_ERR_INVALID_ARG, "null x or y");
+    if (x == y) return fail(SFSEG_ERR_INVALID_ARG, "x and y must not alias");
+    if (int rc = exact_checks(h, tp)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    int terms = 0;
+    if (int rc = exact_terms(h, n_terms, s, &terms)) return rc;
+    float* xt = (float*)h->vbuf[0];
+    float* yt = (float*)h->vbuf[1];
+    launch_exact_in(x, h->g, xt, nullptr, s);
+    SFSEG_LAUNCHED();
+    if (int rc = exact_apply(h, tp, terms, xt, nullptr, yt, nullptr, s)) return rc;
+    launch_exact_out(yt, nullptr, h->g, y, h->flags, s);
+    SFSEG_LAUNCHED();
+    return SFSEG_OK;
+}
+
+int sfseg_power_iterate_exact(sfseg_handle* h, const sfseg_neighborhood* nb, int n_terms, int iters, int init,
+                              float* x_inout, double* norms_out, void* stream) {
+    if (int rc = check_handle(h)) return rc;
+    Taps tp;
+    if (int rc = make_taps(nb, &tp)) return rc;
+    if (!x_inout) return fail(SFSEG_ERR_INVALID_ARG, "null x_inout");
+    if (iters < 0) return fail(SFSEG_ERR_INVALID_ARG, "iters must be >= 0");
+    if (init != SFSEG_INIT_USER && init != SFSEG_INIT_UNIFORM)
+        return fail(SFSEG_ERR_INVALID_ARG, "init must be SFSEG_INIT_USER or SFSEG_INIT_UNIFORM");
+    if (int rc = exact_checks(h, tp)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    int terms = 0;
+    if (int rc = exact_terms(h, n_terms, s, &terms)) return rc;
+    if (int rc = ensure_acc(&h->acc, &h->acc_cap, iters + 2)) return rc;
+    double* acc = h->acc;
+    SFSEG_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (iters + 1), s));
+    float* buf[2] = {(float*)h->vbuf[0], (float*)h->vbuf[1]};
+    launch_exact_in(init == SFSEG_INIT_USER ? x_inout : nullptr, h->g, buf[0], acc, s);
+    SFSEG_LAUNCHED();
+    for (int k = 0; k < iters; ++k)
+        if (int rc = exact_apply(h, tp, terms, buf[k & 1], acc + k, buf[(k + 1) & 1], acc + k + 1, s)) return rc;
+    launch_exact_out(buf[iters & 1], acc + iters, h->g, x_inout, h->flags, s);
+    SFSEG_LAUNCHED();
+    if (norms_out) {
+        std::vector<double> a((size_t)iters + 1);
+        SFSEG_CUDA(cudaMemcpyAsync(a.data(), acc, sizeof(double) * (iters + 1), cudaMemcpyDeviceToHost, s));
+        if (int rc = read_flags(h, s)) return rc;
+        for (int k = 0; k < iters; ++k) norms_out[k] = std::sqrt(a[k + 1]);
+    }
     return SFSEG_OK;
 }
 

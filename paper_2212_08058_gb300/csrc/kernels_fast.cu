@@ -154,6 +154,10 @@ struct Params {
     const float* s;   // separate unary map S_m (SEP kernels), or the state V_k (MODE 5); float32,
                       // internal pitch
     void* out2;       // second output: the record x~ (MODE 4) or Q (MODEs 5 and 6)
+    // MODE 7 only: term j of the exact kernel's series (see below)
+    int exj, exlast;
+    float exc[3];     // c_{3j}, c_{3j+1}, c_{3j+2}
+    float ex_alpha;
 };
 
 // SEP: the unary term u = s^p comes from a separate map S_m (Eq. 9 with its own channels)
@@ -165,7 +169,13 @@ struct Params {
 // G = u^2 B (B the Eq. 7 bracket, so G = u A z for v = u z) and Q, and adds sum V_k B over its
 // voxels to acc_out, with V_k = u x~_k read from P.s (so that <x_k, A z> = s_k sum V_k B needs
 // no division by u).  MODE 6 is the step (MODE 0, the state to out) that also stores s Q to out2:
-// the adjoint's recomputation and Q-pass share the filtering of V_k.  All in the internal layout.
+// the adjoint's recomputation and Q-pass share the filtering of V_k.  MODE 7 serves the exact
+// (Eq. 1) kernel, exp(-a (f_i - f_j)^2) = e^{-a f_i^2} e^{-a f_j^2} sum_n c_n f_i^n f_j^n with
+// c_n = (2a)^n / n!: for the input v = f^{3j} w, its three filtered signals are the series
+// terms n = 3j (G*v), 3j + 1 (G*(f v)) and 3j + 2 (G*(f^2 v)); it adds
+// t = f^{3j} (c_{3j} G*v + f (c_{3j+1} G*(f v) + f c_{3j+2} G*(f^2 v))) to out (writes it when
+// j = 0), and on the last term stores y = u e^{-a f^2} / a * (sum of the terms) and adds |y|^2 to
+// acc_out.  All in the internal layout.
 template <int RT, int RH, int RW, typename TS, typename TVO, bool OUT_X, bool SEP, int MODE>
 __global__ void __launch_bounds__(NTHR, SFSEG_FAST_MINB)
 iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtensorMap mf, Params P) {
@@ -351,14 +361,20 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
         // ---------------- Eq. 7 combination for frame to = tt - RT
         if (to >= t0 && wr < TH) {
             float2 outv[4];
-            float2 outq[(MODE >= 4) ? 4 : 1];
+            float2 outq[(MODE >= 4 && MODE <= 6) ? 4 : 1];
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 const float2 fv = fo[m];
                 const float2 sv = SEP ? so[SEP ? m : 0] : fv;
                 const float2 u = make_float2(unary_pow_fast(sv.x, P.p), unary_pow_fast(sv.y, P.p));
                 const float2 e = fma2(make_float2(-fv.x, -fv.y), fv, f2(P.inv_alpha));   // 1/alpha - f^2
-                if constexpr (MODE == 0 || MODE == 4 || MODE == 6) {
+                if constexpr (MODE == 7) {
+                    float2 F = make_float2(1.f, 1.f);
+                    const float2 f3 = mul2(fv, mul2(fv, fv));
+                    for (int i = 0; i < P.exj; ++i) F = mul2(F, f3);
+                    const float2 inner = fma2(mul2(fv, f2(P.exc[2])), y[1][m], mul2(f2(P.exc[1]), y[2][m]));
+                    outv[m] = mul2(F, fma2(fv, inner, mul2(f2(P.exc[0]), y[0][m])));
+                } else if constexpr (MODE == 0 || MODE == 4 || MODE == 6) {
                     float2 B = fma2(e, y[0][m], make_float2(-y[1][m].x, -y[1][m].y));
                     B = fma2(mul2(f2(2.f), fv), y[2][m], B);
                     const float2 xt = mul2(mul2(s2, u), B);
@@ -393,7 +409,30 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
                     st_pairs(o2, outq, wbase, g.W);
                 }
             }
-            if constexpr (MODE == 1 || MODE == 5) {
+            if constexpr (MODE == 7) {
+                if (h < g.H) {
+                    float* o = reinterpret_cast<float*>(P.out) + ((int64_t)to * g.H + h) * g.pitch + wbase;
+                    if (P.exj > 0) {   // the terms so far
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            if (wbase + 2 * m + 1 < g.W) outv[m] = __fadd2_rn(outv[m], ld_pair(o + 2 * m));
+                            else if (wbase + 2 * m < g.W) outv[m].x += o[2 * m];
+                        }
+                    }
+                    if (P.exlast) {
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            const float2 fv = fo[m];
+                            const float2 a = make_float2(
+                                unary_pow_fast(fv.x, P.p) * expf(-P.ex_alpha * fv.x * fv.x) * P.inv_alpha,
+                                unary_pow_fast(fv.y, P.p) * expf(-P.ex_alpha * fv.y * fv.y) * P.inv_alpha);
+                            outv[m] = mul2(a, outv[m]);
+                            part = fma2(outv[m], outv[m], part);
+                        }
+                    }
+                    st_pairs(o, outv, wbase, g.W);
+                }
+            } else if constexpr (MODE == 1 || MODE == 5) {
                 if (h < g.H) {
                     float* o = reinterpret_cast<float*>(P.out) + ((int64_t)to * g.H + h) * g.pitch + wbase;
                     st_pairs(o, outv, wbase, g.W);
@@ -511,7 +550,7 @@ static int pick_chunk(int T, int tiles, int slots, int rt) {
 template <int RT, int RH, int RW, typename TS, typename TVO, bool OUT_X, bool SEP = false, int MODE = 0>
 static bool launch_t(const void* vin, void* out, const void* f, const Geom& g, const Taps& tp, float inv_alpha,
                      float p, const double* acc_in, double* acc_out, int* flags, cudaStream_t s,
-                     const float* s32 = nullptr, void* out2 = nullptr) {
+                     const float* s32 = nullptr, void* out2 = nullptr, const ExactTerm* ex = nullptr) {
     using C = Cfg<RT, RH, RW, TS, TVO, OUT_X>;
     constexpr bool bf = sizeof(TS) == 2;
     CUtensorMap mv, mf;
@@ -534,6 +573,10 @@ static bool launch_t(const void* vin, void* out, const void* f, const Geom& g, c
     P.f = f;
     P.s = s32;
     P.out2 = out2;
+    P.exj = ex ? ex->j : 0;
+    P.exlast = ex ? ex->last : 0;
+    for (int i = 0; i < 3; ++i) P.exc[i] = ex ? ex->c[i] : 0.f;
+    P.ex_alpha = ex ? ex->alpha : 0.f;
     const int tx = (g.W + TW - 1) / TW, ty = (g.H + TH - 1) / TH;
     P.tchunk = pick_chunk(g.T, tx * ty, slots_per_sm * num_sms(), RT);
     P.acc_in = acc_in;
@@ -591,6 +634,14 @@ static bool dispatch_step_q(const float* vin, float* vout, float* Q, const float
                             float ia, float p, const double* ai, int* fl, cudaStream_t s) {
     return launch_t<RT, RH, RW, float, float, false, false, 6>(vin, vout, f, g, tp, ia, p, ai, nullptr, fl, s, nullptr,
                                                              Q);
+}
+
+// A term of the exact kernel's series (MODE 7), float32 only.
+template <int RT, int RH, int RW>
+static bool dispatch_exact(const float* v, float* y, const float* f, const Geom& g, const Taps& tp, float ia, float p,
+                           const ExactTerm& ex, double* acc_out, int* fl, cudaStream_t s) {
+    return launch_t<RT, RH, RW, float, float, false, false, 7>(v, y, f, g, tp, ia, p, nullptr, acc_out, fl, s, nullptr,
+                                                             nullptr, &ex);
 }
 
 // The adjoint's g-pass in state form (MODE 5), float32 only.
@@ -662,6 +713,16 @@ bool launch_step_q_fast(const float* vin, float* vout, float* Q, const float* f,
 #define SFSEG_GO(A, B, C)                                                                                  \
     if (tp.rt == A && tp.rh == B && tp.rw == C)                                                            \
         return fast::dispatch_step_q<A, B, C>(vin, vout, Q, f, g, tp, inv_alpha, p, acc_in, flags, s);
+    SFSEG_FAST_RADII(SFSEG_GO)
+#undef SFSEG_GO
+    return false;
+}
+
+bool launch_exact_term_fast(const float* v, float* y, const float* f, const Geom& g, const Taps& tp, float inv_alpha,
+                            float p, const ExactTerm& ex, double* acc_out, int* flags, cudaStream_t s) {
+#define SFSEG_GO(A, B, C)                                                                                  \
+    if (tp.rt == A && tp.rh == B && tp.rw == C)                                                            \
+        return fast::dispatch_exact<A, B, C>(v, y, f, g, tp, inv_alpha, p, ex, acc_out, flags, s);
     SFSEG_FAST_RADII(SFSEG_GO)
 #undef SFSEG_GO
     return false;

@@ -56,6 +56,28 @@ bool launch_iterate_fast_ckpt(const float* vin, void* out, bool out_x, const flo
 bool launch_filter_fast(const float* vin, int mode, float* out, float* out2, const float* f, const Geom& g,
                         const Taps& tp, float inv_alpha, float p, const double* acc_in, int* flags, cudaStream_t s);
 
+// One term j of the exact (Eq. 1) kernel's series on the TMA kernel (kernels_fast.cu, mode 7):
+// for the input v = f^{3j} w (internal layout), adds the terms n = 3j, 3j+1, 3j+2 of
+// sum_n c_n f^n G*(f^n w) to y (writes them when j = 0); on the last term multiplies the sum by
+// u e^{-alpha f^2} / alpha and adds ||y||^2 to *acc_out (nullable).  Returns false for a radius
+// without a compiled kernel.
+struct ExactTerm {
+    int j, last;
+    float c[3];     // c_{3j}, c_{3j+1}, c_{3j+2}, c_n = (2 alpha)^n / n! (0 beyond the last term)
+    float alpha;
+};
+bool launch_exact_term_fast(const float* v, float* y, const float* f, const Geom& g, const Taps& tp, float inv_alpha,
+                            float p, const ExactTerm& ex, double* acc_out, int* flags, cudaStream_t s);
+
+// The exact kernel's element-wise parts (kernels_exact.cu, internal layout unless noted): x~ from
+// the caller's x (or 1 everywhere for a null x_user) with acc += ||x~||^2 (nullable); the input
+// of term group j, v = f^{3j} s u e^{-alpha f^2} x~ with s = 1/sqrt(*acc) (or 1); and the
+// caller's x = s y.
+void launch_exact_in(const float* x_user, Geom g, float* xt, double* acc, cudaStream_t s);
+void launch_exact_prep(const float* xt, const double* acc, const float* f32, float alpha, float p, int jt, Geom g,
+                       float* v, int* flags, cudaStream_t s);
+void launch_exact_out(const float* y, const double* acc, Geom g, float* x_user, int* flags, cudaStream_t s);
+
 // The adjoint's recomputing step with its Q-pass (kernels_fast.cu, mode 6): from the state V_k
 // (internal layout, s = 1/sqrt(*acc_in)) writes the next state to vout exactly as the plain step
 // does, and Q = s (a1 c0 - p c1 + a3 c2) of the same filtered signals to Q.  Returns false for a

@@ -55,6 +55,8 @@ SIGNATURES = {
     "sfseg_power_iterate": [_vp, _vp, _i, _fp, _f, ctypes.POINTER(Neighborhood), _i, _i, _vp, _i, _i,
                             _dp, _vp],
     "sfseg_apply": [_vp, ctypes.POINTER(Neighborhood), _vp, _vp, _vp],
+    "sfseg_apply_exact": [_vp, ctypes.POINTER(Neighborhood), _i, _vp, _vp, _vp],
+    "sfseg_power_iterate_exact": [_vp, ctypes.POINTER(Neighborhood), _i, _i, _i, _vp, _dp, _vp],
     "sfseg_rayleigh": [_vp, ctypes.POINTER(Neighborhood), _vp, _dp, _dp, _vp],
     "sfseg_backward": [_vp, ctypes.POINTER(Neighborhood), _vp, _fp, _fp, _vp],
     "sfseg_soft_iou_loss": [_vp, _vp, _vp, _dp, _vp, _vp],
@@ -240,6 +242,33 @@ class PowerIteration:
         y = torch.empty_like(x)
         _check(lib().sfseg_apply(self._h, ctypes.byref(neighborhood(radius, sigma)), _ptr(x), _ptr(y), _stream()))
         return y
+
+    def apply_exact(self, x: torch.Tensor, radius=(2, 7, 7), sigma=None, n_terms: int = 0) -> torch.Tensor:
+        """y = (1/alpha) M x for the exact (Eq. 1) kernel (sfseg_apply_exact; n_terms = 0 picks the
+        series length from alpha and max f, which synchronises)."""
+        self._check_volume(x, "x")
+        y = torch.empty_like(x)
+        _check(lib().sfseg_apply_exact(self._h, ctypes.byref(neighborhood(radius, sigma)), int(n_terms), _ptr(x),
+                                       _ptr(y), _stream()))
+        return y
+
+    def power_iterate_exact(self, radius=(2, 7, 7), sigma=None, iters: int = 50, x: torch.Tensor | None = None,
+                            init: str = "uniform", n_terms: int = 0, return_norms: bool = False):
+        """Power iteration on the exact kernel's operator (sfseg_power_iterate_exact) with the
+        features already set; returns the unit-norm x [T, H, W] (and the norms when asked)."""
+        if init not in ("uniform", "user"):
+            raise ValueError("init must be 'uniform' or 'user'")
+        if x is None:
+            if init == "user":
+                raise ValueError("init='user' needs x")
+            x = torch.empty((self.T, self.H, self.W), device="cuda", dtype=torch.float32)
+        else:
+            self._check_volume(x, "x")
+        norms = np.empty(max(iters, 1)) if return_norms else None
+        _check(lib().sfseg_power_iterate_exact(
+            self._h, ctypes.byref(neighborhood(radius, sigma)), int(n_terms), int(iters), INIT[init], _ptr(x),
+            norms.ctypes.data_as(_dp) if norms is not None else None, _stream()))
+        return (x, norms[:iters]) if return_norms else x
 
     def rayleigh(self, x: torch.Tensor, radius=(2, 7, 7), sigma=None):
         """(rho, residual) of x for the FP32 operator; synchronises."""
