@@ -401,6 +401,88 @@ def bench_separate_maps(sfseg, synth, steps: int = 5):
             "avg_launch_ms": it_ms / max(it_n, 1)}
 
 
+def bench_exact_kernel(sfseg, synth, ref_iters: int = 1500, alphas=(1.0, 0.5, 0.25), study_iters: int = 6000,
+                       checkpoints=(0, 10, 20, 50, 100, 200, 500, 1000, 2000, 4000, 6000)):
+    """The exact (Eq. 1) kernel against its first-order approximation (Sec. 4.3, the Fig. 4
+    study) on the 480p workload (crossing blobs, 64 x 480 x 854, radius (2,7,7), p = 0.1):
+    for each alpha, ref_iters steps of sfseg_power_iterate_exact and of the method (Eq. 7) from
+    the uniform start, their Eq. 3 residuals for their own operators, and the angle and the
+    IoU of the half-maximum masks between the two (equally iterated from the same start: the
+    difference of the operators, not the distance to either eigenvector, whose spectral gap is
+    small here); at the first alpha also the paper's set-up: a reference from study_iters exact
+    steps, then the method's iterations from a non-negative start 70 degrees away from it, with
+    angle and IoU at checkpoints, and both residuals; and the time per exact step."""
+    import numpy as np
+    import torch
+
+    def angle(a, b):
+        a = a.double() / a.double().norm()
+        b = b.double() / b.double().norm()
+        return float(np.degrees(2.0 * torch.asin(torch.clamp((a - b).norm() / 2.0, max=1.0)).item()))
+
+    def iou(a, b):
+        ma, mb = a > 0.5 * a.max(), b > 0.5 * b.max()
+        return float((ma & mb).sum().item() / max(1, (ma | mb).sum().item()))
+
+    def residual(y, x):
+        y, x = y.double(), x.double()
+        rho = float((x * y).sum() / (x * x).sum())
+        return float((y - rho * x).norm() / (abs(rho) * x.norm()))
+
+    V = torch.from_numpy(synth.crossing_blobs(T, H, W, seed=SEED)).cuda()
+    sweep, out = [], {}
+    for ai, alpha in enumerate(alphas):
+        h = sfseg.PowerIteration(1, T, H, W, alpha=alpha)
+        h.set_features(V)
+        x = torch.empty((T, H, W), device="cuda")
+        h.power_iterate_exact(RADIUS, iters=2, x=x)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        xe = h.power_iterate_exact(RADIUS, iters=ref_iters, x=x).clone()
+        e1.record()
+        torch.cuda.synchronize()
+        xm = h.power_iterate(None, radius=RADIUS, iters=ref_iters).clone()
+        sweep.append({"alpha": alpha, "exact_residual": residual(h.apply_exact(xe, RADIUS), xe),
+                      "method_residual": residual(h.apply(xm, RADIUS), xm),
+                      "angle_deg": angle(xm, xe), "iou_half_max": iou(xm, xe)})
+        if ai == 0:
+            out["exact_ms_per_step"] = e0.elapsed_time(e1) / ref_iters
+            # series length as the library picks it (tail bound of the series below 2^-24)
+            xb = 2.0 * alpha * float(V.max().item()) ** 2
+            tail, terms = xb * np.exp(xb), 1
+            while tail > 2.0 ** -24:
+                tail *= xb / (terms + 1)
+                terms += 1
+            out["exact_series_terms"] = terms
+            # the reference for the 70-degree study: study_iters exact steps
+            xe = h.power_iterate_exact(RADIUS, iters=study_iters - ref_iters, x=xe.contiguous(), init="user").clone()
+            ref_res = residual(h.apply_exact(xe, RADIUS), xe)
+            # a non-negative start 70 degrees from xe: xe + t r, r noise away from the objects
+            gen = torch.Generator(device="cuda").manual_seed(SEED)
+            r = torch.rand((T, H, W), device="cuda", generator=gen) * (1.0 - xe / xe.max()) ** 4
+            lo, hi = 0.0, 1.0
+            while angle(xe + hi * r, xe) < 70.0:
+                hi *= 2.0
+            for _ in range(60):
+                mid = 0.5 * (lo + hi)
+                lo, hi = (mid, hi) if angle(xe + mid * r, xe) < 70.0 else (lo, mid)
+            xt = (xe + hi * r).contiguous()
+            curve, done = [], 0
+            for c in checkpoints:
+                if c > done:
+                    xt = h.power_iterate(None, radius=RADIUS, iters=c - done, x=xt, init="user")
+                    done = c
+                curve.append([c, angle(xt, xe), iou(xt, xe)])
+            out["method_from_70_degrees"] = {
+                "alpha": alpha, "reference_exact_iterations": study_iters, "reference_residual": ref_res,
+                "method_residual_at_end": residual(h.apply(xt, RADIUS), xt),
+                "columns": ["iterations", "angle_deg", "iou_half_max"], "rows": curve}
+        h.close()
+    out["alpha_sweep"] = {"iterations": ref_iters, "rows": sweep}
+    return {"workload": "crossing blobs C=1 fp32 64x480x854, radius (2,7,7), p 0.1", **out}
+
+
 def bench_online(sfseg, synth, q: int = 13, iters: int = 10, frames: int = 64):
     """Online form (Sec. 4.5) on the 480p crossing-blobs stream: a 13-frame sub-window (the
     paper's t = 6 either side of a frame), 10 iterations per incoming frame.  Frames per second
@@ -454,6 +536,7 @@ EXTRAS = {
     "adjoint": lambda sf, sy: bench_adjoint(sf, sy, steps=1),
     "small_graphs": lambda sf, sy: bench_small_graphs(sf, sy),
     "r133_storage": lambda sf, sy: bench_r133_storage(sf, sy, steps=2),
+    "exact_kernel": lambda sf, sy: bench_exact_kernel(sf, sy),
     "time_to_residual": lambda sf, sy, ws: bench_time_to_residual(sf, sy, ws),
 }
 
@@ -600,6 +683,7 @@ def main():
             out["adjoint"] = bench_adjoint(sfseg, synth)
             out["small_graphs"] = bench_small_graphs(sfseg, synth)
             out["r133_storage"] = bench_r133_storage(sfseg, synth)
+            out["exact_kernel"] = bench_exact_kernel(sfseg, synth)
             out["time_to_residual"] = bench_time_to_residual(sfseg, synth, warmstart)
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline()
