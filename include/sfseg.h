@@ -44,7 +44,7 @@ typedef enum sfseg_status {
     SFSEG_ERR_NONFINITE = 7,   /* a feature is negative, NaN or Inf, or a norm became non-finite */
     SFSEG_ERR_ZERO_NORM = 8,   /* an iterate became exactly zero (e.g. u = 0 everywhere) */
     SFSEG_ERR_STATE = 9,       /* call order violated (no features set, no recorded forward, ...) */
-    SFSEG_ERR_UNSUPPORTED = 10 /* valid request this build does not implement */
+    SFSEG_ERR_UNSUPPORTED = 10 /* valid request the library does not implement */
 } sfseg_status;
 
 typedef enum sfseg_dtype {

@@ -200,6 +200,41 @@ def test_kronecker_closed_form():
     np.testing.assert_allclose(nu[-1], lam, rtol=1e-12)
 
 
+def test_exact_kernel_kronecker_closed_form():
+    """Eq. 1 with constant f: the pair term is exp(0) = 1 for every alpha, so M = u^2 G_t (x)
+    G_h (x) G_w with the top eigenpair u^2 l_t l_h l_w, v_t (x) v_h (x) v_w (1D dense
+    eigensolvers); and at two voxels with known features one entry is
+    u_i u_j exp(-alpha (f_i - f_j)^2) exp(-d^2 / (2 sigma^2)) per axis."""
+    T, H, W = 4, 7, 9
+    r = (1, 2, 3)
+    sig = (0.9, 1.3, 1.7)
+    fval, p, alpha = 0.55, 0.2, 1.7
+    f = np.full((T, H, W), fval)
+
+    def band(n, ra, sa):
+        d = np.arange(n)[:, None] - np.arange(n)[None, :]
+        return np.where(np.abs(d) <= ra, np.exp(-d * d / (2 * sa * sa)), 0.0)
+
+    vals, vecs = [], []
+    for n, ra, sa in zip((T, H, W), r, sig):
+        e, V = np.linalg.eigh(band(n, ra, sa))
+        vals.append(e[-1])
+        vecs.append(V[:, -1] * np.sign(V[:, -1].sum()))
+    lam = fval ** (2 * p) * vals[0] * vals[1] * vals[2]
+    v = np.einsum("a,b,c->abc", *vecs).ravel()
+    Me = oracle.affinity(f, f, p, alpha, r, sigma=sig, exact=True)
+    np.testing.assert_allclose(Me @ v, lam * v, rtol=0, atol=1e-13 * lam)
+    # one entry with distinct features: voxel (1, 3, 4) and its neighbour (2, 2, 6)
+    g = np.linspace(0.1, 0.9, T * H * W).reshape(T, H, W)
+    Mg = oracle.affinity(g, g, p, alpha, r, sigma=sig, exact=True)
+    i = np.ravel_multi_index((1, 3, 4), (T, H, W))
+    j = np.ravel_multi_index((2, 2, 6), (T, H, W))
+    want = (g.flat[i] * g.flat[j]) ** p * np.exp(-alpha * (g.flat[i] - g.flat[j]) ** 2) * \
+        np.exp(-1 / (2 * sig[0] ** 2) - 1 / (2 * sig[1] ** 2) - 4 / (2 * sig[2] ** 2))
+    assert abs(Mg[i, j] - want) <= 1e-14 * want
+    assert Mg[i, j] == Mg[j, i]
+
+
 def test_diagonal_special_case():
     """Radius (0, 0, 0): M = diag(u_i^2), so K steps from the uniform start give exactly
     u^(2K) / ||u^(2K)|| (catches a wrong exponent p, e.g. s^(2p) for the unary term)."""

@@ -38,6 +38,10 @@ MUTANTS = [
      "orc_spmv(N, rowptr, col, val, x_out, y);\n        double nu = 0.0;\n"
      "        for (int64_t q = 0; q < N; ++q) nu += fabs(y[q]);",
      ["test_two_node_closed_form", "test_power_iteration_matches_dense_eigensolver"]),
+    ("eq1_pair_not_squared", "exp(-alpha * df * df)", "exp(-alpha * fabs(df))",
+     ["test_exact_kernel_kronecker_closed_form"]),
+    ("eq1_pair_sign", "exp(-alpha * df * df)", "exp(alpha * df * df)",
+     ["test_exact_kernel_kronecker_closed_form", "test_exact_kernel_approaches_taylor"]),
     ("binarize_no_max_scaling", "exp(-gain * (y[i] / m - center))", "exp(-gain * (y[i] - center))",
      ["test_soft_binarize_kronecker_closed_form"]),
     ("binarize_sigmoid_sign", "exp(-gain * (y[i] / m - center))", "exp(gain * (y[i] / m - center))",
