@@ -12,9 +12,10 @@
 //      the 128 threads); it walks down the 5 + 2rh input rows once, forms the three signals z1 = v, z2 = f^2 v, z3 = f v of each, and accumulates
 //      them into its 5 x 3 outputs with packed FP32 FMAs (FFMA2, one per column pair).
 //   3. w-pass: a thread takes 8 output columns of one row; it loads its window of the h-pass
-//      result once (aligned float2 pairs; the odd-aligned pairs are rebuilt in registers) and
-//      feeds the three w-filtered signals straight into the t-filter, kept in registers in
-//      transposed direct form (2rt running partial sums per value, no frame ring to index).
+//      result once as aligned float2 pairs (the odd-aligned pairs are rebuilt in registers at
+//      rw > 4; at rw <= 4 their taps run as two scalar FMAs instead) and feeds the three
+//      w-filtered signals straight into the t-filter, kept in registers in transposed direct
+//      form (2rt running partial sums per value, no frame ring to index).
 //   4. Eq. 7 combination for the frame rt behind, the Eq. 8 norm partial and the store of the
 //      next state.
 // The h-pass result is double-buffered and the epilogue reads f from global memory, so a frame
@@ -344,8 +345,13 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
                         const int q = 2 * m + d + C::ODD;
-                        const float2 in = (q & 1) ? make_float2(pa[q >> 1].y, pa[(q >> 1) + 1].x) : pa[q >> 1];
-                        acc[d & 1][m] = fma2(in, gd, acc[d & 1][m]);
+                        if ((q & 1) && RW <= 4) {   // odd-aligned pair: two scalar FMAs
+                            acc[d & 1][m].x = fmaf(pa[q >> 1].y, gd.x, acc[d & 1][m].x);
+                            acc[d & 1][m].y = fmaf(pa[(q >> 1) + 1].x, gd.x, acc[d & 1][m].y);
+                        } else {
+                            const float2 in = (q & 1) ? make_float2(pa[q >> 1].y, pa[(q >> 1) + 1].x) : pa[q >> 1];
+                            acc[d & 1][m] = fma2(in, gd, acc[d & 1][m]);
+                        }
                     }
                 }
 #pragma unroll
