@@ -28,7 +28,7 @@ def _worker(rank, world, port, out):
 
 def test_two_rank_aggregation():
     world = 2
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # no fork of a process that may run threads
     out = mgr.dict()
     mp.spawn(_worker, args=(world, _free_port(), out), nprocs=world, join=True)
     v0, ms0, s0 = out[0]
