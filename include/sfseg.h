@@ -312,19 +312,23 @@ int sfseg_selftest_wait(sfseg_handle* h, long long spins, void* stream);
  * grad_x, iters, iters_bf16, init, the recording, neighbourhood, the handle's buffers) captures
  * it, later ones replay it.  The graph runs on a stream of the handle,
  * ordered after the work already queued on the caller's stream and before the work queued
- * after the call; results are identical.  Worth it for small volumes, where launch latency
- * dominates.  Off by default. */
+ * after the call; results are those of direct launches (up to the order of the FP64 atomic
+ * sums of norms and dot products, as between any two runs).  Worth it for small volumes, where
+ * launch latency dominates.  Off by default.  Errors: INVALID_ARG (null handle); capture
+ * failures surface as CUDA from the call that captures. */
 int sfseg_enable_graphs(sfseg_handle* h, int on);
 
 /* Instrumentation (no counterpart in the paper).  When enabled, each sfseg_power_iterate call
  * records two CUDA events on its stream, before its first and after its last iteration-kernel
  * launch.  sfseg_iter_timing waits for the recorded events, returns the summed milliseconds and
  * the number of iteration launches they bracket (host outputs), and resets both.  Disabled by
- * default; enabling it adds two event records per call. */
+ * default; enabling it adds two event records per call.  Errors: INVALID_ARG (null handle or
+ * output), CUDA. */
 int sfseg_enable_iter_timing(sfseg_handle* h, int on);
 int sfseg_iter_timing(sfseg_handle* h, double* ms, int64_t* launches);
 
-/* Number of CUDA kernels this library has launched in the process so far (host output). */
+/* Number of CUDA kernels this library has launched in the process so far (host output).
+ * Errors: INVALID_ARG (null count). */
 int sfseg_kernel_launches(int64_t* count);
 
 /* No-allocation power iteration (the paper has no counterpart: this is a deployment aid).
