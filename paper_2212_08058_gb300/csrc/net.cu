@@ -8,13 +8,14 @@
 // Activations are bf16 in channels-last layout [T][H][W][C]; every convolution is an implicit
 // GEMM on the 5th-generation tensor cores (tcgen05.mma, kind::f16, bf16 x bf16 -> fp32 in TMEM):
 //   D[v, co] = sum_{tap, ci} X[v + tap, ci] W[co, tap, ci],   M = 128 voxels of one row along w,
-//   N = output channels, K = 16 input channels per instruction, 27 taps x C_in/16 instructions.
+//   K = 16 input channels per instruction.  Each input row is read once: its 9 (dt, dw) taps x
+//   C_in/16 MMAs each carry the three taps along h at once (N = 3 x output channels, D over the
+//   accumulators of the three output rows it feeds, a ring of blocks in TMEM).
 // The A operand is read straight from a TMA-filled ring of input rows in the canonical
 // no-swizzle K-major layout ([8-channel chunk][3 frames][130 voxels][8 channels]); a tap's shift
-// along w is a 16-byte offset of the descriptor's start address, along t a 2080-byte offset,
-// along h another ring slot.  All weights of the layer stay in shared memory.  One warp issues
-// the TMA copies, one the MMAs, four read the accumulator from TMEM (double-buffered) and run
-// the epilogue.  The backward pass reuses the same kernel for the data gradient (flipped taps,
+// along w is a 16-byte offset of the descriptor's start address, along t a 2080-byte offset.
+// All weights of the layer stay in shared memory.  One warp issues the TMA copies, one the MMAs,
+// four read each finished row's accumulator from TMEM, zero it, and run the epilogue.  The backward pass reuses the same kernel for the data gradient (flipped taps,
 // transposed channels, ReLU mask in the epilogue); the weight gradient is a reduction over
 // voxels on the CUDA cores.
 #include <cuda.h>
@@ -39,7 +40,6 @@ constexpr int CHUNK_BYTES = (CHUNK_DATA + 127) / 128 * 128;   // its stride (128
 #define SFSEG_NET_NSLOT 4
 #endif
 constexpr int NSLOT = SFSEG_NET_NSLOT;  // input-row ring (rows in flight ahead of the MMAs: NSLOT - 2)
-constexpr int NBAR = 2 * NSLOT + 6;     // full[NSLOT], empty[NSLOT], accf[2], acce[2], wbar, drain
 constexpr int NTHR = 192;               // 6 warps
 constexpr int HR = 32;                  // output rows per CTA
 constexpr long long kSpin = 1ll << 26;
@@ -133,6 +133,32 @@ __device__ __forceinline__ void tmem_ld<16>(uint32_t t, uint32_t (&r)[16]) {
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
         : "r"(t));
 }
+
+// Writes zeros to N columns of this warp's 32 TMEM lanes starting at taddr.
+template <int N>
+__device__ __forceinline__ void tmem_zero(uint32_t t);
+template <>
+__device__ __forceinline__ void tmem_zero<32>(uint32_t t) {
+    const uint32_t z = 0u;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
+        ::"r"(t), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z),
+          "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z),
+          "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z)
+        : "memory");
+}
+template <>
+__device__ __forceinline__ void tmem_zero<16>(uint32_t t) {
+    const uint32_t z = 0u;
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};"
+        ::"r"(t), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z), "r"(z),
+          "r"(z), "r"(z), "r"(z), "r"(z)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 struct ConvArgs {
@@ -145,14 +171,26 @@ struct ConvArgs {
     int* flags;
 };
 
+// The three taps along h of one (dt, dw, ks) share one MMA: an input row h' feeds the output
+// rows h' + 1, h', h' - 1 through the weights of dh = 0, 1, 2, so B stacks the three weight
+// blocks along N (N = 3 COUT) and D spans the accumulators of three output rows.  The
+// accumulators form a ring of R blocks of COUT columns over all 512 TMEM columns; output row j
+// uses block (-j) mod R, so the rows i, i - 1, i - 2 fed by input row i sit in consecutive
+// blocks (an MMA is split in two where the ring wraps, and trimmed at the tile's first and last
+// rows).  A block is zeroed when its row has been read, so every MMA accumulates.
 template <int CIN, int COUT>
 struct ConvCfg {
     static constexpr int NCH = CIN / 8;                       // 8-channel chunks of A
     static constexpr int KS = CIN / 16;                       // MMAs per tap
     static constexpr int SLOT_BYTES = NCH * CHUNK_BYTES;
     static constexpr int WBYTES = 27 * KS * 2 * COUT * 16;    // packed weights
-    static constexpr int SMEM = WBYTES + NSLOT * SLOT_BYTES + NBAR * 8 + 16 + 128;
-    static constexpr int TMEM_COLS = COUT <= 16 ? 32 : 64;    // two accumulator buffers
+    static constexpr int TMEM_COLS = 512;
+    static constexpr int R = TMEM_COLS / COUT;                // accumulator blocks in the ring
+    static constexpr int NB = 2 * NSLOT + 2 * R + 2;          // full, empty, accf[R], acce[R], wbar, drain
+    // at least 120 KB so that one CTA holds the SM's tensor memory alone
+    static constexpr int SMEM_NEED = WBYTES + NSLOT * SLOT_BYTES + NB * 8 + 16 + 128;
+    static constexpr int SMEM = SMEM_NEED > 120 * 1024 ? SMEM_NEED : 120 * 1024;
+    static_assert(R >= 4 && 3 * COUT <= 256 && COUT % 16 == 0, "accumulator ring");
 };
 
 template <int CIN, int COUT, int EPI>
@@ -164,13 +202,13 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
     unsigned char* wsm = sm;                                   // weights
     unsigned char* ring = sm + C::WBYTES;                      // NSLOT input rows
     uint64_t* bar = reinterpret_cast<uint64_t*>(ring + NSLOT * C::SLOT_BYTES);
-    uint64_t* full = bar;                    // [NSLOT]
-    uint64_t* empty = bar + NSLOT;           // [NSLOT]
-    uint64_t* accf = bar + 2 * NSLOT;        // [2]
-    uint64_t* acce = bar + 2 * NSLOT + 2;    // [2]
-    uint64_t* wbar = bar + 2 * NSLOT + 4;
-    uint64_t* drain = bar + 2 * NSLOT + 5;   // completion of this CTA's MMAs, awaited after a timeout
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + NBAR);
+    uint64_t* full = bar;                        // [NSLOT]
+    uint64_t* empty = bar + NSLOT;               // [NSLOT]
+    uint64_t* accf = bar + 2 * NSLOT;            // [R]: the row in accumulator block b is complete
+    uint64_t* acce = bar + 2 * NSLOT + C::R;     // [R]: block b has been read and zeroed
+    uint64_t* wbar = bar + 2 * NSLOT + 2 * C::R;
+    uint64_t* drain = wbar + 1;                  // completion of this CTA's MMAs, awaited after a timeout
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + C::NB);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // work item: (t, w segment, row range)
@@ -188,7 +226,7 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
             mb_init(&full[i], 1);
             mb_init(&empty[i], 1);
         }
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < C::R; ++i) {
             mb_init(&accf[i], 1);
             mb_init(&acce[i], 4);
         }
@@ -206,6 +244,16 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    auto blk = [&](int j) { return (C::R - j % C::R) % C::R; };   // accumulator block of output row j
+    if (warp >= 2) {   // the epilogue warps zero the whole ring (their lane quadrants) once
+        const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+#pragma unroll 1
+        for (int b = 0; b < C::R; ++b) tmem_zero<COUT>(tmem + lanes + (uint32_t)(b * COUT));
+        tmem_st_wait();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 
     int issued = 0;                  // producer: input rows requested so far
     if (warp == 0) {
@@ -222,43 +270,42 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {   // ---------------- MMA issuer
+        if (lane == 0) {   // ---------------- MMA issuer: one group of MMAs per input row
             bool ok = mb_wait(wbar, 0, a.flags);
-            const uint32_t id = idesc_bf16(COUT);
             const uint32_t wbase = su32(wsm), rbase = su32(ring);
-            for (int j = 0; ok && j < nout; ++j) {
-                if (j == 0) ok = mb_wait(&full[0], 0, a.flags) && mb_wait(&full[1], 0, a.flags);
-                ok = ok && mb_wait(&full[(j + 2) % NSLOT], (uint32_t)(((j + 2) / NSLOT) & 1), a.flags);
-                const int b = j & 1;
-                if (ok && j >= 2) ok = mb_wait(&acce[b], (uint32_t)((j / 2 - 1) & 1), a.flags);
+            constexpr uint32_t TILE = 2 * 3 * COUT * 16;          // stacked B tile of one (dt, dw, ks)
+            for (int i = 0; ok && i < nin; ++i) {
+                ok = mb_wait(&full[i % NSLOT], (uint32_t)((i / NSLOT) & 1), a.flags);
+                // output rows fed by input row i: j = i - dh for dh = 0, 1, 2, within [0, nout)
+                const int jhi = min(i, nout - 1), jlo = max(i - 2, 0);
+                // row i enters the ring: its block must have been read back from row i - R
+                if (ok && i < nout && i >= C::R)
+                    ok = mb_wait(&acce[blk(i)], (uint32_t)(((i - C::R) / C::R) & 1), a.flags);
                 if (!ok) break;
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(b * (C::TMEM_COLS / 2));
-                uint32_t accum = 0;
-#pragma unroll 1
-                for (int dh = 0; dh < 3; ++dh) {
-                    const uint32_t slot = rbase + (uint32_t)(((j + dh) % NSLOT) * C::SLOT_BYTES);
-                    // Descriptors of this input row and of the taps with this dh; the rest of
-                    // each operand's start address is a compile-time offset added to the
-                    // start-address field (addresses stay below 256 KB and 16-byte aligned, so
-                    // the field, (address mod 2^18) / 16, never carries).
-                    const uint64_t a0 = sdesc(slot, CHUNK_BYTES, 128);
-                    const uint64_t b0 = sdesc(wbase + (uint32_t)(dh * 3 * C::KS * 2 * COUT * 16), COUT * 16, 128);
+                const int dh0 = i - jhi, nrow = jhi - jlo + 1;
+                const int b0 = blk(jhi);
+                const int n1 = min(nrow, C::R - b0), n2 = nrow - n1;   // before and after the wrap
+                const uint32_t id1 = idesc_bf16(n1 * COUT), id2 = idesc_bf16((n2 > 0 ? n2 : 1) * COUT);
+                const uint32_t d1 = tmem + (uint32_t)(b0 * COUT), d2 = tmem;
+                const uint64_t a0 = sdesc(rbase + (uint32_t)((i % NSLOT) * C::SLOT_BYTES), CHUNK_BYTES, 128);
+                // B of rows dh0 .. and of the rows after the wrap: same tiles, later start rows
+                const uint64_t bA = sdesc(wbase + (uint32_t)(dh0 * COUT * 16), 3 * COUT * 16, 128);
+                const uint64_t bB = sdesc(wbase + (uint32_t)((dh0 + n1) * COUT * 16), 3 * COUT * 16, 128);
 #pragma unroll
-                    for (int dt = 0; dt < 3; ++dt)
+                for (int dt = 0; dt < 3; ++dt)
 #pragma unroll
-                        for (int dw = 0; dw < 3; ++dw) {
+                    for (int dw = 0; dw < 3; ++dw) {
 #pragma unroll
-                            for (int ks = 0; ks < C::KS; ++ks) {
-                                const uint64_t ad = a0 + (uint64_t)((2 * ks * CHUNK_BYTES + dt * RW * 16 + dw * 16) >> 4);
-                                const uint64_t bd = b0 + (uint64_t)((((dt * 9 + dw) * C::KS + ks) * 2 * COUT * 16) >> 4);
-                                umma(d, ad, bd, id, accum);
-                                accum = 1;
-                            }
+                        for (int ks = 0; ks < C::KS; ++ks) {
+                            const uint64_t ad = a0 + (uint64_t)((2 * ks * CHUNK_BYTES + dt * RW * 16 + dw * 16) >> 4);
+                            const uint64_t toff = (uint64_t)((((dt * 3 + dw) * C::KS + ks) * TILE) >> 4);
+                            umma(d1, ad, bA + toff, id1, 1u);
+                            if (n2 > 0) umma(d2, ad, bB + toff, id2, 1u);
                         }
-                }
-                umma_commit(&accf[b]);
-                umma_commit(&empty[j % NSLOT]);
+                    }
+                umma_commit(&empty[i % NSLOT]);
+                if (i >= 2 && i - 2 < nout) umma_commit(&accf[blk(i - 2)]);
             }
         }
     } else {   // ---------------- epilogue: warps 2..5
@@ -266,12 +313,15 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
         const int v = q * 32 + lane;     // voxel within the tile
         const int w = w0 + v;
         for (int j = 0; j < nout; ++j) {
-            const int b = j & 1;
-            const bool ok = mb_wait(&accf[b], (uint32_t)((j / 2) & 1), a.flags);
+            const int b = blk(j);
+            const bool ok = mb_wait(&accf[b], (uint32_t)((j / C::R) & 1), a.flags);
             tc_fence_after();
             uint32_t r[COUT];
-            tmem_ld<COUT>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * (C::TMEM_COLS / 2)), r);
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * COUT);
+            tmem_ld<COUT>(taddr, r);
             tmem_ld_wait();
+            tmem_zero<COUT>(taddr);      // the block's next row accumulates from zero
+            tmem_st_wait();
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mb_arrive(&acce[b]);
@@ -356,8 +406,9 @@ __global__ void to_channels_last(const TIn* f, int C, const float* extra, int64_
 }
 
 // Pack fp32 weights W[co][27][ci] (co < cout, ci < cin) into the B-operand layout
-// [tap][ks][chunk(2)][COUTP][8] bf16 with zero padding to COUTP x CINP; `flip` packs the
-// data-gradient kernel instead: W'[ci][tap][co] = W[co][26 - tap][ci].
+// [dt][dw][ks][chunk(2)][dh][COUTP][8] bf16 with zero padding to COUTP x CINP (tap =
+// 9 dt + 3 dh + dw): each (dt, dw, ks) tile stacks the three dh blocks along N; `flip` packs
+// the data-gradient kernel instead: W'[ci][tap][co] = W[co][26 - tap][ci].
 __global__ void pack_weights(const float* W, int cout, int cin, int COUTP, int CINP, int flip, __nv_bfloat16* out) {
     const int KS = CINP / 16;
     const int total = 27 * KS * 2 * COUTP * 8;
@@ -365,9 +416,12 @@ __global__ void pack_weights(const float* W, int cout, int cin, int COUTP, int C
         int r = idx;
         const int e = r % 8; r /= 8;
         const int n = r % COUTP; r /= COUTP;
+        const int dh = r % 3; r /= 3;
         const int ch = r % 2; r /= 2;
         const int ks = r % KS; r /= KS;
-        const int tap = r;
+        const int dw = r % 3; r /= 3;
+        const int dt = r;
+        const int tap = 9 * dt + 3 * dh + dw;
         const int k = ks * 16 + ch * 8 + e;     // input-channel index of the packed conv
         float v = 0.f;
         if (!flip) {
