@@ -312,6 +312,11 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
         const int q = warp & 3;          // TMEM lane quadrant of this warp
         const int v = q * 32 + lane;     // voxel within the tile
         const int w = w0 + v;
+        // the bias in registers, read once (the output stores may alias it as far as the compiler
+        // knows, which would otherwise reload it for every row)
+        float bz[EPI == EPI_LAST ? 1 : (EPI == EPI_RELU ? COUT : 1)];
+#pragma unroll
+        for (int c = 0; c < (int)(sizeof(bz) / sizeof(float)); ++c) bz[c] = EPI == EPI_MASK ? 0.f : a.bias[c];
         for (int j = 0; j < nout; ++j) {
             const int b = blk(j);
             const bool ok = mb_wait(&accf[b], (uint32_t)((j / C::R) & 1), a.flags);
@@ -330,7 +335,7 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
             if (w >= a.W) continue;
             const int64_t vox = ((int64_t)t * a.H + h) * a.W + w;
             if constexpr (EPI == EPI_LAST) {
-                const float z = __uint_as_float(r[0]) + a.bias[0];
+                const float z = __uint_as_float(r[0]) + bz[0];
                 reinterpret_cast<float*>(a.out)[vox] = z;
                 a.out2[vox] = z > 20.f ? z : log1pf(expf(z));   // softplus
             } else {
@@ -338,8 +343,8 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
                 if constexpr (EPI == EPI_RELU) {
 #pragma unroll
                     for (int c = 0; c < COUT / 2; ++c) {
-                        const float x0 = fmaxf(__uint_as_float(r[2 * c]) + a.bias[2 * c], 0.f);
-                        const float x1 = fmaxf(__uint_as_float(r[2 * c + 1]) + a.bias[2 * c + 1], 0.f);
+                        const float x0 = fmaxf(__uint_as_float(r[2 * c]) + bz[2 * c], 0.f);
+                        const float x1 = fmaxf(__uint_as_float(r[2 * c + 1]) + bz[2 * c + 1], 0.f);
                         o[c] = __floats2bfloat162_rn(x0, x1);
                     }
                 } else {   // EPI_MASK: dL/dz of the layer below = dL/da * [a > 0]
