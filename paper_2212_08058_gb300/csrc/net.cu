@@ -41,7 +41,9 @@ constexpr int CHUNK_BYTES = (CHUNK_DATA + 127) / 128 * 128;   // its stride (128
 #endif
 constexpr int NSLOT = SFSEG_NET_NSLOT;  // input-row ring (rows in flight ahead of the MMAs: NSLOT - 2)
 constexpr int NTHR = 192;               // 6 warps
-constexpr int HR = 32;                  // output rows per CTA
+// Output rows per CTA: the tallest of 64, 32, 16 that still gives the grid 4 waves (taller
+// tiles load fewer halo rows and amortise each CTA's weight copy and TMEM set-up).
+constexpr int kHrChoices[3] = {64, 32, 16};
 constexpr long long kSpin = 1ll << 26;
 
 enum Epi { EPI_RELU = 0, EPI_LAST = 1, EPI_MASK = 2 };
@@ -163,6 +165,7 @@ __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.
 
 struct ConvArgs {
     int T, H, W;
+    int HR;                       // output rows per CTA
     const __nv_bfloat16* wpack;   // packed weights (layout of the smem B operand)
     const float* bias;            // [COUT] or null
     void* out;                    // EPI_RELU/EPI_MASK: bf16 [T][H][W][COUT]; EPI_LAST: float z [T][H][W]
@@ -212,6 +215,7 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     // work item: (t, w segment, row range)
+    const int HR = a.HR;
     const int nws = (a.W + MT - 1) / MT, nhr = (a.H + HR - 1) / HR;
     int item = blockIdx.x;
     const int hr = item % nhr;
@@ -654,7 +658,12 @@ int run_conv(const void* in, int T, int H, int W, const __nv_bfloat16* wpack, co
     ConvArgs a;
     a.T = T; a.H = H; a.W = W;
     a.wpack = wpack; a.bias = bias; a.out = out; a.out2 = out2; a.mask = mask; a.flags = flags;
-    const int items = T * ((W + MT - 1) / MT) * ((H + HR - 1) / HR);
+    int items = 0;
+    for (int hr : kHrChoices) {
+        a.HR = hr;
+        items = T * ((W + MT - 1) / MT) * ((H + hr - 1) / hr);
+        if (items >= 4 * num_sms()) break;
+    }
     k<<<items, NTHR, Cf::SMEM, s>>>(m, a);
     count_launches(1);
     NET_CUDA(cudaGetLastError());
