@@ -1,7 +1,8 @@
 """Plain FP64 CPU oracle for the SFSeg / SFSeg++ power iteration (arXiv 2212.08058).
 
-TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline
-leg of ``bench.py`` may import this package.  It shares no code with the CUDA library
+TEST INFRASTRUCTURE ONLY.  Only the test suite (with ``tests/golden/make_golden.py``),
+``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg and ``--impl reference`` arm may
+import this package.  It shares no code with the CUDA library
 (``paper_2212_08058_gb300``) and never imports it; both sides receive the same seeded inputs
 from ``paper_2212_08058_gb300.synth``, which holds no arithmetic of the method.
 
