@@ -158,7 +158,7 @@ def cpu_baseline(seconds_budget: float = 20.0):
     one = time.perf_counter() - t0
     k = max(1, min(ITERS, int(seconds_budget / max(one, 1e-3))))
     t0 = time.perf_counter()
-    oracle.power_filter(f, f, 0.1, 1.0, RADIUS, start, k)
+    x_oracle, _ = oracle.power_filter(f, f, 0.1, 1.0, RADIUS, start, k)
     dt = time.perf_counter() - t0
     nvox = T * H * W
     out = {"value": nvox * k / dt, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
@@ -187,7 +187,20 @@ def cpu_baseline(seconds_budget: float = 20.0):
     out["csr_small"] = {"value": fb.size * 20 / t_iter, "unit": UNIT, "nnz": int(M.nnz),
                         "build_s": t_build, "cores": threads,
                         "sample": "explicit Eq. 2 matrix of the 8x64x64 drifting blob, radius (1,3,3), 20 iterations"}
-    return out
+    return out, x_oracle, k
+
+
+def parity_stats(x_gpu, x_ref, tol: float):
+    """Max-abs error of a unit-norm GPU iterate against the oracle's at equal iteration count,
+    also relative to max |x| and times sqrt(N), and the angle between the two in degrees."""
+    import numpy as np
+    a = np.asarray(x_gpu, dtype=np.float64).reshape(-1)
+    b = np.asarray(x_ref, dtype=np.float64).reshape(-1)
+    d = float(np.abs(a - b).max())
+    ua, ub = a / np.linalg.norm(a), b / np.linalg.norm(b)
+    ang = float(np.degrees(2.0 * np.arcsin(min(1.0, np.linalg.norm(ua - ub) / 2.0))))
+    return {"max_abs": d, "max_abs_over_max_x": d / float(np.abs(b).max()), "max_abs_times_sqrt_n": d * np.sqrt(a.size),
+            "angle_deg": ang, "tolerance_max_abs": tol, "within_tolerance": d <= tol}
 
 
 def run_reference(args, rank, world):
@@ -219,7 +232,7 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
-def bench_bf16_multichannel(sfseg, synth, steps: int = 10):
+def bench_bf16_multichannel(sfseg, synth, steps: int = 10, with_parity: bool = True):
     """SFSeg++ with bf16 storage: C = 8 bf16 channels of 64 x 480 x 854 (the multichannel recipe,
     drawn on the device), radius (2,7,7), 50 iterations all in bf16 storage.  Device-resident
     voxel-iterations/s, CUDA events."""
@@ -240,12 +253,27 @@ def bench_bf16_multichannel(sfseg, synth, steps: int = 10):
     e1.record()
     torch.cuda.synchronize()
     it_ms, it_n = h.iter_timing()
-    h.close()
     nvox = T * H * W
-    return {"workload": "SFSeg++ C=8 bf16 64x480x854, radius (2,7,7), 50 iterations in bf16 storage",
-            "value": nvox * ITERS * steps / (e0.elapsed_time(e1) * 1e-3), "unit": UNIT,
-            "avg_launch_ms": it_ms / max(it_n, 1),
-            "hbm_frac_of_measured": 6.0 * nvox / (it_ms * 1e-3 / max(it_n, 1)) / 1e9 / _peaks()[0]}
+    out = {"workload": "SFSeg++ C=8 bf16 64x480x854, radius (2,7,7), 50 iterations in bf16 storage",
+           "value": nvox * ITERS * steps / (e0.elapsed_time(e1) * 1e-3), "unit": UNIT,
+           "avg_launch_ms": it_ms / max(it_n, 1),
+           "hbm_frac_of_measured": 6.0 * nvox / (it_ms * 1e-3 / max(it_n, 1)) / 1e9 / _peaks()[0]}
+    if with_parity:
+        # the error of this result: the same volume and schedule against the FP64 oracle on the
+        # bf16 channels widened exactly, at a bounded iteration count (the oracle takes about
+        # half a second per iteration of this volume on the host cores)
+        import numpy as np
+        import oracle
+        k = 10
+        xg = h.power_iterate(V, w, 0.0, RADIUS, iters=k, iters_bf16=k, x=x).cpu().numpy()
+        V64 = V.float().cpu().numpy().astype(np.float64)
+        f = oracle.combine(V64, w.astype(np.float64), 0.0)
+        del V64
+        xo, _ = oracle.power_filter(f, f, 0.1, 1.0, RADIUS, np.ones(f.shape), k)
+        out["parity"] = {"iterations": k, "vs": "FP64 oracle on the same bf16 channels, uniform start",
+                         **parity_stats(xg, xo, 2e-3)}
+    h.close()
+    return out
 
 
 def bench_soft_binarize(sfseg, synth, steps: int = 5, tail: int = 10):
@@ -367,10 +395,25 @@ def bench_adjoint(sfseg, synth, steps: int = 5):
         t_bwd += e1.elapsed_time(e2)
     h.close()
     nvox = Tb * Hb * Wb
+    # the reverse pass's algorithmic work per step: two filterings of Eq. 7's three signals (the
+    # recomputing step with its Q-pass, and the g-pass), 2 x 3 x 17 FMA per voxel at (1,3,3), and
+    # 72 bytes per voxel (recomputing step: read V_k, f, write V_{k+1}, Q_x; g-pass: read v_g, f,
+    # V_k, write G, Q_g; element-wise pass: read f, v_g, Q_x, V_k, Q_g, G, gz, write gz, v_g)
+    fma_step, bytes_step = 2 * 3 * 17, 72.0
+    t_b = t_bwd / steps * 1e-3
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    alu_peak = nsm * 128 * 2 * 2070e6 / 1e12
+    ach = 2.0 * fma_step * nvox * K / t_b / 1e12
+    hbm = bytes_step * nvox * K / t_b / 1e9
     return {"workload": "C=8 fp32 32x240x427, radius (1,3,3), 30 iterations, checkpoint every 5, 1 - soft-IoU",
             "forward_ms": t_fwd / steps, "loss_and_backward_ms": t_bwd / steps,
             "backward_over_forward": t_bwd / max(t_fwd, 1e-9),
-            "forward_voxel_iterations_per_s": nvox * K / (t_fwd / steps * 1e-3)}
+            "forward_voxel_iterations_per_s": nvox * K / (t_fwd / steps * 1e-3),
+            "roofline": {"bound": "alu", "achieved": ach, "peak": alu_peak, "unit": "TFLOP/s", "frac": ach / alu_peak,
+                         "peak_kind": f"derived: {nsm} SMs x 128 FP32 lanes x 2 flop x 2070 MHz",
+                         "algorithmic": "per reverse step: 2 filterings x 51 FMA + 72 B per voxel "
+                                        "(whole loss + backward time, all 30 steps)",
+                         "hbm": {"achieved": hbm, "peak": _peaks()[0], "unit": "GB/s", "frac": hbm / _peaks()[0]}}}
 
 
 def bench_separate_maps(sfseg, synth, steps: int = 5):
@@ -507,23 +550,26 @@ def bench_online(sfseg, synth, q: int = 13, iters: int = 10, frames: int = 64):
             "window_voxel_iterations_per_s": frames * q * H * W * iters / (ms * 1e-3)}
 
 
-def bench_time_to_residual(sfseg, synth, warmstart, tol: float = 1e-4):
+def bench_time_to_residual(sfseg, synth, warmstart, tol: float = 1e-4, repeats: int = 3):
     """Wall time to the Eq. 3 residual tol on the C = 8 bf16 120 x 1080 x 1920 volume from four
     starts: uniform and S_m with float32 storage (the plain method), the coarse-to-fine start
     (two coarser levels), and the trained network's refinement of it followed by bf16 storage
-    until the residual reaches 2e-3, then float32."""
+    until the residual reaches 2e-3, then float32.  Each start is timed `repeats` times in turn:
+    median and the sorted runs."""
     import torch
     T5, H5, W5 = 120, 1080, 1920
     V, _ = synth.multichannel_torch(T5, H5, W5, 8, seed=5500, device="cuda", dtype=torch.bfloat16)
     w = synth.fixed_weights(8)
     net = sfseg.WarmStartNet(9)
     trained = warmstart.load(net)
-    res = warmstart.compare_starts(V, w, RADIUS, tol=tol, net=net if trained else None, max_iters=3000)
+    res = warmstart.compare_starts(V, w, RADIUS, tol=tol, net=net if trained else None, max_iters=3000,
+                                   repeats=repeats)
     net.close()
     del V
     torch.cuda.empty_cache()
     res["volume"] = "C=8 bf16 120x1080x1920 (multichannel recipe on the device), radius (2,7,7)"
     res["tol"] = tol
+    res["repeats"] = repeats
     res["warmstart_trained"] = trained
     return res
 
@@ -595,6 +641,7 @@ def main():
         step(feats, x)
     torch.cuda.synchronize()
     n_launch0 = sfseg.kernel_launches()
+    tma0, gen0, _ = sfseg.iterate_kernel_stats()
 
     # ---- device-resident timed region
     h.enable_iter_timing(True)
@@ -611,6 +658,10 @@ def main():
         torch.cuda.synchronize()
     ms = ev0.elapsed_time(ev1)
     launches = sfseg.kernel_launches() - n_launch0
+    tma1, gen1, kernel_name = sfseg.iterate_kernel_stats()
+    if gen1 != gen0 or tma1 - tma0 != args.steps * ITERS:
+        raise RuntimeError(f"the timed steps did not all run on the TMA kernel: {tma1 - tma0} TMA steps, "
+                           f"{gen1 - gen0} generic-stencil steps for {args.steps * ITERS} iterations")
     clk_summary = clk.summary()
     it_ms, it_n = h.iter_timing()
     h.enable_iter_timing(False)
@@ -660,7 +711,7 @@ def main():
                        "l2": "inputs larger than L2 (f + two iterate buffers = 318 MB > 129 MB)"},
             "roofline": {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": alu_achieved / alu_peak, "traffic": profiled_traffic(),
-                         "kernel": "iter_fast<2,7,7,float,float>",
+                         "kernel": kernel_name,
                          "peak_kind": f"derived: {nsm} SMs x 128 FP32 lanes x 2 flop x {clk:.0f} MHz",
                          "algorithmic_flops_per_launch": 2.0 * FMA_PER_VOXEL * nvox,
                          "avg_launch_ms": per_launch_s * 1e3,
@@ -669,6 +720,8 @@ def main():
             "e2e": {"value": evalue, "unit": UNIT, "h2d_bytes_per_step": nvox * 4,
                     "d2h_bytes_per_step": nvox * 4},
             "gpu_launches": launches,
+            "kernel_ran": {"iteration_kernel": kernel_name, "tma_steps": tma1 - tma0,
+                           "generic_stencil_steps": gen1 - gen0},
             "clocks": clk_summary,
             "residual": res, "rho": rho,
             "paper_context": "0.01 s per iteration per 480x854 frame on a GTX Titan X (Maxwell), "
@@ -686,7 +739,12 @@ def main():
             out["exact_kernel"] = bench_exact_kernel(sfseg, synth)
             out["time_to_residual"] = bench_time_to_residual(sfseg, synth, warmstart)
         if world == 1 and not args.no_cpu_baseline:
-            out["cpu_baseline"] = cpu_baseline()
+            out["cpu_baseline"], x_oracle, k = cpu_baseline()
+            # the error of the timed result: the GPU iterate after the oracle's iteration count,
+            # same volume and uniform start, against the oracle's
+            xg = h.power_iterate(feats, radius=RADIUS, iters=k, x=x).cpu().numpy()
+            out["parity"] = {"iterations": k, "vs": "FP64 oracle (filter form), same volume, uniform start",
+                             **parity_stats(xg, x_oracle, 1e-5)}
         print(json.dumps(out), flush=True)
     h.close()
     if world > 1:

@@ -285,6 +285,38 @@ int sfseg_net_backward(sfseg_net* net, const void* features, int dtype, int C, c
                        int T, int H, int W, const float* target, double* loss, float* grads_out,
                        void* stream);
 
+/* One layer of the network alone, on a caller's activation (to run the network layer by layer,
+ * or to check one layer's convolution against a reference).  layer = 0..3.
+ *   in    device bf16 [T][H][W][CP] channels-last, CP = 16 for layer 0 (its c_in channels, then
+ *         zeros) and 32 for layers 1..3.
+ *   out   layers 0..2: device bf16 [T][H][W][32] = ReLU(conv(in) + b), rounded to nearest;
+ *         layer 3: device float32 [T][H][W] z = conv(in) + b, and out2 (device float32
+ *         [T][H][W], required) = softplus(z).
+ * conv is the 3x3x3 cross-correlation with zero padding 1 and the layer's weights rounded to
+ * bf16, accumulated in fp32 on the tensor cores.  Asynchronous; a bounded wait that gave up is
+ * reported by sfseg_net_check.  Errors: INVALID_ARG, SHAPE, CUDA. */
+int sfseg_net_layer_forward(sfseg_net* net, int layer, const void* in, int T, int H, int W,
+                            void* out, float* out2, void* stream);
+
+/* Gradients of one layer given the loss gradient dz at its output before the activation
+ * (device bf16 [T][H][W][DP], DP = 32 for layers 0..2; 16 for layer 3, whose one output is
+ * channel 0 and the other 15 channels must be 0), and the layer's input `in` (as for
+ * sfseg_net_layer_forward):
+ *   dW_out  device float32 [COUT][27][CIN] (overwritten): sum over voxels of dz x in(shifted);
+ *   db_out  device float32 [COUT] (overwritten): sum over voxels of dz;
+ *   dx_out  layers 1..3: device bf16 [T][H][W][32] or NULL: the gradient at the pre-activation
+ *           of the layer below, conv^T(dz) * [in > 0] (flipped taps, bf16 weights, fp32
+ *           accumulation on the tensor cores); must be NULL for layer 0.
+ * COUT = 32 (1 for layer 3), CIN = the network's c_in for layer 0, else 32.  Asynchronous.
+ * Errors: INVALID_ARG, SHAPE, CUDA. */
+int sfseg_net_layer_backward(sfseg_net* net, int layer, const void* in, const void* dz, int T,
+                             int H, int W, void* dx_out, float* dW_out, float* db_out,
+                             void* stream);
+
+/* Synchronises `stream` and returns TIMEOUT if a bounded wait inside one of the network's
+ * kernels gave up since the last check (then clears the flag), else OK. */
+int sfseg_net_check(sfseg_net* net, void* stream);
+
 /* One AdamW step (decoupled weight decay) with the gradients of the last sfseg_net_backward. */
 int sfseg_net_adamw(sfseg_net* net, float lr, float beta1, float beta2, float eps,
                     float weight_decay, void* stream);
@@ -331,6 +363,16 @@ int sfseg_iter_timing(sfseg_handle* h, double* ms, int64_t* launches);
  * Errors: INVALID_ARG (null count). */
 int sfseg_kernel_launches(int64_t* count);
 
+/* Which kernel ran the power-iteration steps (instrumentation; no counterpart in the paper).
+ * The radii (1,3,3), (2,7,7), (1,4,4) and (1,2,2) run on the TMA-staged stencil kernel; other
+ * radii, or a volume whose tensor maps the driver does not encode, run on the generic streaming
+ * stencil, which gives the same results more slowly.  Process-wide counts of steps issued on
+ * each (host outputs; steps captured into a CUDA graph count once, at capture), and in
+ * last_kernel (host buffer of len >= 1 chars, or NULL) the kernel name of the last step,
+ * e.g. "iter_fast<2,7,7,float,float>".  Errors: INVALID_ARG (null count). */
+int sfseg_iterate_kernel_stats(int64_t* tma_steps, int64_t* generic_steps, char* last_kernel,
+                               int len);
+
 /* No-allocation power iteration (the paper has no counterpart: this is a deployment aid).
  *
  * For callers that cannot allocate device memory -- a server that reserves its whole memory
@@ -347,6 +389,10 @@ int sfseg_kernel_launches(int64_t* count);
  *   Arguments: as sfseg_create (prm, C, T, H, W) and sfseg_power_iterate (features, dtype,
  *   weights, bias, nb, iters, x_inout, init, norms_out, stream).  The caller owns features,
  *   x_inout and norms_out.
+ *   Errors found on the device (TIMEOUT, NONFINITE for bad features or a non-finite norm,
+ *   ZERO_NORM) are reported only by a call that passes norms_out: that call synchronises and
+ *   reads the device's error flags.  A call without norms_out returns once its work is queued
+ *   and reports only argument and launch errors; the next call clears the flags it left.
  *   Sharing: every call, from any thread, on any stream of the same device, uses the same
  *   array, which keeps the previous call's contents (the call clears what must start at
  *   zero).  Calls whose GPU work overlaps -- concurrent streams, or calls on one device from

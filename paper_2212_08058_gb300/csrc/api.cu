@@ -195,7 +195,7 @@ static int check_handle(sfseg_handle* h) {
     return SFSEG_OK;
 }
 
-static int make_taps(const sfseg_neighborhood* nb, Taps* tp) {
+int sfseg::make_taps(const sfseg_neighborhood* nb, Taps* tp) {
     if (!nb) return fail(SFSEG_ERR_INVALID_ARG, "null neighborhood");
     if (nb->rt < 0 || nb->rh < 0 || nb->rw < 0 || nb->rt > kMaxRT || nb->rh > kMaxRH || nb->rw > kMaxRW)
         return fail(SFSEG_ERR_SHAPE, "radius out of range (0 <= rt <= 4, 0 <= rh, rw <= 8)");
@@ -570,6 +570,13 @@ int sfseg_warmstart(sfseg_handle* h, sfseg_net* net, const void* features, int d
 int sfseg_kernel_launches(int64_t* count) {
     if (!count) return fail(SFSEG_ERR_INVALID_ARG, "null argument");
     *count = launches_so_far();
+    return SFSEG_OK;
+}
+
+int sfseg_iterate_kernel_stats(int64_t* tma_steps, int64_t* generic_steps, char* last_kernel, int len) {
+    if (!tma_steps || !generic_steps) return fail(SFSEG_ERR_INVALID_ARG, "null argument");
+    if (last_kernel && len < 1) return fail(SFSEG_ERR_INVALID_ARG, "len must be >= 1");
+    iterate_kernel_stats(tma_steps, generic_steps, last_kernel, len);
     return SFSEG_OK;
 }
 

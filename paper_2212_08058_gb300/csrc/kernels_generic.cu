@@ -16,6 +16,8 @@
 // for a global reduction, and z1 = v needs no power in the halo.
 #include <atomic>
 #include <cstdio>
+#include <cstring>
+#include <mutex>
 
 #include "common.cuh"
 #include "launch.h"
@@ -100,6 +102,31 @@ struct OpApply {
 };
 
 static std::atomic<int64_t> g_launches{0};
+// Which kernel ran the power-iteration steps: counts of steps issued on the TMA kernel and on the
+// generic stencil, and the name of the last step's kernel instantiation.
+static std::atomic<int64_t> g_steps_tma{0}, g_steps_generic{0};
+static std::mutex g_step_mu;
+static char g_step_name[96] = "";
+
+static void note_step(bool tma, const Taps& tp, int vin_type, int out_type, bool out_x, bool record, bool sep) {
+    (tma ? g_steps_tma : g_steps_generic).fetch_add(1, std::memory_order_relaxed);
+    char buf[96];
+    std::snprintf(buf, sizeof(buf), "%s<%d,%d,%d,%s,%s%s%s>", tma ? "iter_fast" : "stream_stencil<OpIter>", tp.rt,
+                  tp.rh, tp.rw, vin_type == kF32 ? "float" : "bf16",
+                  out_x ? "float(caller x)" : (out_type == kBF16 ? "bf16" : "float"), record ? ",record" : "",
+                  sep ? ",separate maps" : "");
+    std::lock_guard<std::mutex> lk(g_step_mu);
+    std::memcpy(g_step_name, buf, sizeof(buf));
+}
+
+void iterate_kernel_stats(int64_t* tma_steps, int64_t* generic_steps, char* name, int len) {
+    if (tma_steps) *tma_steps = g_steps_tma.load(std::memory_order_relaxed);
+    if (generic_steps) *generic_steps = g_steps_generic.load(std::memory_order_relaxed);
+    if (name && len > 0) {
+        std::lock_guard<std::mutex> lk(g_step_mu);
+        std::snprintf(name, (size_t)len, "%s", g_step_name);
+    }
+}
 void count_launches(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 int64_t launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
@@ -139,12 +166,19 @@ void launch_iterate(const void* vin, int vin_type, void* out, int out_type, bool
     // The TMA kernel serves the method's radii, recording steps (float32, shared maps) included.
     if (ckpt == nullptr && fast_iterate_supported(tp) &&
         launch_iterate_fast(vin, vin_type, out, out_type, out_x, f, g, tp, inv_alpha, p, acc_in, acc_out, flags, s,
-                            s32))
+                            s32)) {
+        note_step(true, tp, vin_type, out_type, out_x, false, s32 != nullptr);
         return;
+    }
     if (ckpt != nullptr && vin_type == kF32 && s32 == nullptr && fast_iterate_supported(tp) &&
         launch_iterate_fast_ckpt((const float*)vin, out, out_x, (const float*)f, g, tp, inv_alpha, p, acc_in, acc_out,
-                                 ckpt, flags, s))
+                                 ckpt, flags, s)) {
+        note_step(true, tp, vin_type, out_type, out_x, true, false);
         return;
+    }
+    // Radii without a TMA kernel, or a tensor map the driver would not encode: the generic
+    // streaming stencil (same results, slower); counted so that callers can tell.
+    note_step(false, tp, vin_type, out_type, out_x, ckpt != nullptr, s32 != nullptr);
 #define SFSEG_IT(TVI, TVO, TF, OX) \
     iterate_t<TVI, TVO, TF, OX>(vin, out, f, ckpt, g, tp, inv_alpha, p, acc_in, acc_out, flags, s, s32)
     // A step of the bf16 phase reads v and f in bf16 and writes bf16, or float32 when the next

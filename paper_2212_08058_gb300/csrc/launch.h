@@ -8,6 +8,7 @@
 #include "common.cuh"
 
 struct sfseg_handle;
+struct sfseg_neighborhood;
 
 namespace sfseg {
 
@@ -163,8 +164,17 @@ void launch_soft_iou(const float* x, const float* tgt, int64_t n, float* grad, d
 
 int num_sms();
 
+// Validates a neighbourhood (radius limits; sigma finite and > 0 where its radius is > 0) and
+// fills the three 1D Gaussian tap arrays exp(-d^2 / (2 sigma^2)), d = -r..r (all 1 at r = 0).
+// Returns SFSEG_OK, or INVALID_ARG / SHAPE with the thread's last-error message set (api.cu).
+int make_taps(const sfseg_neighborhood* nb, Taps* tp);
+
 // Records `msg` as the thread's sfseg_last_error() text and returns `code`.
 int set_last_error(int code, const char* msg);
+
+// Process-wide counts of power-iteration steps issued on the TMA kernel and on the generic
+// stencil, and the kernel name of the last one (sfseg_iterate_kernel_stats).
+void iterate_kernel_stats(int64_t* tma_steps, int64_t* generic_steps, char* name, int len);
 
 // Process-wide count of kernels launched by the library (sfseg_kernel_launches).
 void count_launches(int n);

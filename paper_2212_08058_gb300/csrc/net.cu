@@ -729,17 +729,23 @@ int net_forward(sfseg_net* n, const void* feats, int dtype, int C, const float* 
     return SFSEG_OK;
 }
 
-int wgrad(sfseg_net* n, int l, const __nv_bfloat16* dz, int dzc, const __nv_bfloat16* x, int xc, int T, int H, int W,
-          cudaStream_t s) {
+// dW (float32 [cout][27][cin]) and db (float32 [cout]) of layer l accumulated from dz (bf16
+// [N][dzc]) and the layer's input x (bf16 [N][xc]).
+int wgrad_into(int l, int cin, const __nv_bfloat16* dz, int dzc, const __nv_bfloat16* x, int xc, int T, int H, int W,
+               float* dW, float* db, cudaStream_t s) {
     const int64_t N = (int64_t)T * H * W;
     int splits = (int)((N + 4095) / 4096);
     if (splits > 24) splits = 24;
     if (splits < 1) splits = 1;
-    wgrad_kernel<<<dim3(27, splits), 1024, 0, s>>>(dz, dzc, kCout[l], x, xc, layer_cin(n, l), T, H, W,
-                                                   n->g + n->off[2 * l], n->g + n->off[2 * l + 1]);
+    wgrad_kernel<<<dim3(27, splits), 1024, 0, s>>>(dz, dzc, kCout[l], x, xc, cin, T, H, W, dW, db);
     count_launches(1);
     NET_CUDA(cudaGetLastError());
     return SFSEG_OK;
+}
+
+int wgrad(sfseg_net* n, int l, const __nv_bfloat16* dz, int dzc, const __nv_bfloat16* x, int xc, int T, int H, int W,
+          cudaStream_t s) {
+    return wgrad_into(l, layer_cin(n, l), dz, dzc, x, xc, T, H, W, n->g + n->off[2 * l], n->g + n->off[2 * l + 1], s);
 }
 
 uint64_t splitmix(uint64_t& x) {
@@ -891,6 +897,49 @@ int sfseg_net_backward(sfseg_net* n, const void* features, int dtype, int C, con
     *loss = 1.0 - a[0] / std::sqrt(a[1] * a[2]);
     if (grads_out) NET_CUDA(cudaMemcpy(grads_out, n->g, n->np * 4, cudaMemcpyDeviceToHost));
     return SFSEG_OK;
+}
+
+int sfseg_net_layer_forward(sfseg_net* n, int layer, const void* in, int T, int H, int W, void* out, float* out2,
+                            void* stream) {
+    if (!n || !in || !out) return nfail(SFSEG_ERR_INVALID_ARG, "null argument");
+    if (layer < 0 || layer > 3) return nfail(SFSEG_ERR_INVALID_ARG, "layer must be in [0, 3]");
+    if (layer == 3 && !out2) return nfail(SFSEG_ERR_INVALID_ARG, "the last layer needs out2 (softplus output)");
+    if (T < 1 || H < 1 || W < 1) return nfail(SFSEG_ERR_SHAPE, "empty volume");
+    if ((int64_t)T * H * W >= (int64_t(1) << 31)) return nfail(SFSEG_ERR_SHAPE, "volume too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (int rc = pack_all(n, s)) return rc;
+    const float* b = n->p + n->off[2 * layer + 1];
+    const __nv_bfloat16* x = (const __nv_bfloat16*)in;
+    if (layer == 0) return run_conv<16, 32, EPI_RELU>(x, T, H, W, n->wf[0], b, out, nullptr, nullptr, n->flags, s);
+    if (layer < 3) return run_conv<32, 32, EPI_RELU>(x, T, H, W, n->wf[layer], b, out, nullptr, nullptr, n->flags, s);
+    return run_conv<32, 16, EPI_LAST>(x, T, H, W, n->wf[3], b, out, out2, nullptr, n->flags, s);
+}
+
+int sfseg_net_layer_backward(sfseg_net* n, int layer, const void* in, const void* dz, int T, int H, int W,
+                             void* dx_out, float* dW_out, float* db_out, void* stream) {
+    if (!n || !in || !dz || !dW_out || !db_out) return nfail(SFSEG_ERR_INVALID_ARG, "null argument");
+    if (layer < 0 || layer > 3) return nfail(SFSEG_ERR_INVALID_ARG, "layer must be in [0, 3]");
+    if (T < 1 || H < 1 || W < 1) return nfail(SFSEG_ERR_SHAPE, "empty volume");
+    if ((int64_t)T * H * W >= (int64_t(1) << 31)) return nfail(SFSEG_ERR_SHAPE, "volume too large");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (int rc = pack_all(n, s)) return rc;
+    const int cin = layer_cin(n, layer), cinp = layer == 0 ? 16 : 32, dzc = layer == 3 ? 16 : 32;
+    const __nv_bfloat16* x = (const __nv_bfloat16*)in;
+    const __nv_bfloat16* g = (const __nv_bfloat16*)dz;
+    NET_CUDA(cudaMemsetAsync(dW_out, 0, (size_t)kCout[layer] * 27 * cin * sizeof(float), s));
+    NET_CUDA(cudaMemsetAsync(db_out, 0, (size_t)kCout[layer] * sizeof(float), s));
+    if (int rc = wgrad_into(layer, cin, g, dzc, x, cinp, T, H, W, dW_out, db_out, s)) return rc;
+    if (dx_out && layer > 0) {
+        if (layer == 3)
+            return run_conv<16, 32, EPI_MASK>(g, T, H, W, n->wb[3], nullptr, dx_out, nullptr, x, n->flags, s);
+        return run_conv<32, 32, EPI_MASK>(g, T, H, W, n->wb[layer], nullptr, dx_out, nullptr, x, n->flags, s);
+    }
+    return SFSEG_OK;
+}
+
+int sfseg_net_check(sfseg_net* n, void* stream) {
+    if (!n) return nfail(SFSEG_ERR_INVALID_ARG, "null net");
+    return check_flags(n, (cudaStream_t)stream);
 }
 
 int sfseg_net_adamw(sfseg_net* n, float lr, float beta1, float beta2, float eps, float weight_decay, void* stream) {

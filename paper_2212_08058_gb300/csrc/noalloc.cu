@@ -85,22 +85,8 @@ extern "C" int sfseg_power_iterate_noalloc(const sfseg_params* prm, int C, int T
                                          std::to_string(padded) + " > " + std::to_string(kMaxPadded));
     if (iters < 0 || iters > kMaxIters)
         return fail(SFSEG_ERR_INVALID_ARG, "iters must be in [0, " + std::to_string(kMaxIters) + "]");
-    if (nb->rt < 0 || nb->rh < 0 || nb->rw < 0 || nb->rt > kMaxRT || nb->rh > kMaxRH || nb->rw > kMaxRW)
-        return fail(SFSEG_ERR_SHAPE, "radius out of range (0 <= rt <= 4, 0 <= rh, rw <= 8)");
-    const float sg[3] = {nb->sigma_t, nb->sigma_h, nb->sigma_w};
-    const int rr[3] = {nb->rt, nb->rh, nb->rw};
     Taps tp;
-    std::memset(&tp, 0, sizeof(tp));
-    tp.rt = nb->rt;
-    tp.rh = nb->rh;
-    tp.rw = nb->rw;
-    float* dst[3] = {tp.gt, tp.gh, tp.gw};
-    for (int a = 0; a < 3; ++a) {
-        if (rr[a] > 0 && !(sg[a] > 0.f && std::isfinite(sg[a])))
-            return fail(SFSEG_ERR_INVALID_ARG, "sigma must be finite and > 0 where the radius is > 0");
-        for (int d = -rr[a]; d <= rr[a]; ++d)
-            dst[a][d + rr[a]] = rr[a] == 0 ? 1.f : (float)std::exp(-(double)d * d / (2.0 * (double)sg[a] * sg[a]));
-    }
+    if (int rc = make_taps(nb, &tp)) return rc;
     if (C > 1)
         for (int c = 0; c < C; ++c)
             if (!std::isfinite(weights[c])) return fail(SFSEG_ERR_INVALID_ARG, "non-finite channel weight");

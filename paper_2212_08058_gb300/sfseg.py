@@ -73,6 +73,8 @@ SIGNATURES = {
     "sfseg_enable_iter_timing": [_vp, _i],
     "sfseg_iter_timing": [_vp, _dp, ctypes.POINTER(ctypes.c_int64)],
     "sfseg_kernel_launches": [ctypes.POINTER(ctypes.c_int64)],
+    "sfseg_iterate_kernel_stats": [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                   ctypes.c_char_p, _i],
     "sfseg_net_create": [_i, ctypes.c_uint64, ctypes.POINTER(_vp)],
     "sfseg_net_destroy": [_vp],
     "sfseg_net_num_params": [_vp, ctypes.POINTER(ctypes.c_int64)],
@@ -81,6 +83,9 @@ SIGNATURES = {
     "sfseg_net_forward": [_vp, _vp, _i, _i, _vp, _i, _i, _i, _vp, _vp],
     "sfseg_net_backward": [_vp, _vp, _i, _i, _vp, _i, _i, _i, _vp, _dp, _fp, _vp],
     "sfseg_net_adamw": [_vp, _f, _f, _f, _f, _f, _vp],
+    "sfseg_net_layer_forward": [_vp, _i, _vp, _i, _i, _i, _vp, _vp, _vp],
+    "sfseg_net_layer_backward": [_vp, _i, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp],
+    "sfseg_net_check": [_vp, _vp],
     "sfseg_warmstart": [_vp, _vp, _vp, _i, _vp, _vp, _vp],
     "sfseg_power_iterate_noalloc": [ctypes.POINTER(Params), _i, _i, _i, _i, _vp, _i, _fp, _f,
                                     ctypes.POINTER(Neighborhood), _i, _vp, _i, _dp, _vp],
@@ -469,12 +474,52 @@ class WarmStartNet:
               weight_decay: float = 0.0):
         _check(lib().sfseg_net_adamw(self._n, lr, beta1, beta2, eps, weight_decay, _stream()))
 
+    def layer_forward(self, layer: int, x: torch.Tensor):
+        """One layer on a channels-last bf16 activation x [T, H, W, 16 or 32]: bf16 [T, H, W, 32]
+        for layers 0..2, (z, softplus(z)) float32 [T, H, W] for layer 3."""
+        assert x.dtype == torch.bfloat16 and x.is_contiguous() and x.dim() == 4
+        T, H, W, _ = x.shape
+        if layer < 3:
+            out = torch.empty((T, H, W, 32), device=x.device, dtype=torch.bfloat16)
+            _check(lib().sfseg_net_layer_forward(self._n, layer, _ptr(x), T, H, W, _ptr(out), None, _stream()))
+            return out
+        z = torch.empty((T, H, W), device=x.device, dtype=torch.float32)
+        x0 = torch.empty_like(z)
+        _check(lib().sfseg_net_layer_forward(self._n, layer, _ptr(x), T, H, W, _ptr(z), _ptr(x0), _stream()))
+        return z, x0
+
+    def layer_backward(self, layer: int, x: torch.Tensor, dz: torch.Tensor, want_dx: bool = True):
+        """Gradients of one layer: (dx bf16 [T, H, W, 32] or None, dW float32 [COUT, 3, 3, 3, CIN],
+        db float32 [COUT]) for its input x and the gradient dz at its pre-activation output."""
+        assert x.dtype == torch.bfloat16 and dz.dtype == torch.bfloat16
+        T, H, W, _ = x.shape
+        cout, cin = (1, 32) if layer == 3 else (32, self.c_in if layer == 0 else 32)
+        dW = torch.empty((cout, 3, 3, 3, cin), device=x.device, dtype=torch.float32)
+        db = torch.empty((cout,), device=x.device, dtype=torch.float32)
+        dx = torch.empty((T, H, W, 32), device=x.device, dtype=torch.bfloat16) if (want_dx and layer > 0) else None
+        _check(lib().sfseg_net_layer_backward(self._n, layer, _ptr(x.contiguous()), _ptr(dz.contiguous()), T, H, W,
+                                              _ptr(dx), _ptr(dW), _ptr(db), _stream()))
+        return dx, dW, db
+
+    def check(self):
+        """Synchronise; raise TIMEOUT if a bounded wait in the network's kernels gave up."""
+        _check(lib().sfseg_net_check(self._n, _stream()))
+
 
 def kernel_launches() -> int:
     """Kernels launched by libsfseg.so in this process so far."""
     n = ctypes.c_int64()
     _check(lib().sfseg_kernel_launches(ctypes.byref(n)))
     return n.value
+
+
+def iterate_kernel_stats():
+    """(steps on the TMA kernel, steps on the generic stencil, name of the last step's kernel),
+    process-wide."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    buf = ctypes.create_string_buffer(128)
+    _check(lib().sfseg_iterate_kernel_stats(ctypes.byref(a), ctypes.byref(b), buf, len(buf)))
+    return a.value, b.value, buf.value.decode()
 
 
 class SFSegFunction(torch.autograd.Function):

@@ -127,14 +127,16 @@ def load(net: sfseg.WarmStartNet, path: str = DEFAULT_WEIGHTS) -> bool:
 
 def compare_starts(feats: torch.Tensor, w, radius=(2, 7, 7), tol: float = 1e-4, net=None, chunk: int = 20,
                    max_iters: int = 4000, bf16_until: float = 2e-3, levels: int = 2, coarse_tol: float = COARSE_TOL,
-                   kinds=("uniform", "smap", "coarse", "net"), adaptive: bool = True):
+                   kinds=("uniform", "smap", "coarse", "net"), adaptive: bool = True, repeats: int = 1):
     """Wall time (CUDA events around the whole run: coarse solves, the network and every residual
     check included) to reach residual <= tol on the volume from
       uniform_f32       the uniform start, float32 storage (the plain method),
       smap_f32          the S_m start (Alg. 1 line 3), float32 storage,
       coarse_f32        the coarse-to-fine start (sfseg_coarse_start), float32 storage,
       warmstart_bf16    the network's refinement of the coarse start, bf16 storage until the
-                        residual reaches bf16_until, then float32 (when a network is given)."""
+                        residual reaches bf16_until, then float32 (when a network is given).
+    With repeats > 1 the starts are timed in turn that many times; each entry then also gives the
+    sorted times of its repeats ("ms_runs") and "ms" is their median."""
     C, T, H, W = feats.shape
     out = {}
     with sfseg.PowerIteration(C, T, H, W) as h:
@@ -147,24 +149,32 @@ def compare_starts(feats: torch.Tensor, w, radius=(2, 7, 7), tol: float = 1e-4, 
         if net is not None:
             runs.append(("warmstart_bf16", "net", bf16_until))
         runs = [r for r in runs if r[1] in kinds]
-        for name, kind, b16 in runs:
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            coarse_its = None
-            init = "user"
-            if kind in ("coarse", "net"):
-                x, coarse_its = h.coarse_start(radius, levels=levels, tol=coarse_tol)
-                if kind == "net":
-                    x = h.warmstart(net, feats, x)
-            else:
-                init = kind
-            x, its, res, trace = iterate_to_residual(h, radius, x, tol, chunk, max_iters, b16, init, adaptive)
-            e1.record()
-            torch.cuda.synchronize()
-            out[name] = {"ms": e0.elapsed_time(e1), "iterations": its, "residual": res,
-                         "coarse_iterations": coarse_its,
-                         "trace": [(int(a), float(b)) for a, b in trace[:: max(1, len(trace) // 12)]]}
+        for rep in range(repeats):
+            for name, kind, b16 in runs:
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                coarse_its = None
+                init = "user"
+                if kind in ("coarse", "net"):
+                    x, coarse_its = h.coarse_start(radius, levels=levels, tol=coarse_tol)
+                    if kind == "net":
+                        x = h.warmstart(net, feats, x)
+                else:
+                    init = kind
+                x, its, res, trace = iterate_to_residual(h, radius, x, tol, chunk, max_iters, b16, init, adaptive)
+                e1.record()
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1)
+                if rep == 0:
+                    out[name] = {"ms": ms, "iterations": its, "residual": res, "coarse_iterations": coarse_its,
+                                 "trace": [(int(a), float(b)) for a, b in trace[:: max(1, len(trace) // 12)]],
+                                 "ms_runs": [ms]}
+                else:
+                    out[name]["ms_runs"].append(ms)
+        for v in out.values():
+            v["ms_runs"].sort()
+            v["ms"] = float(np.median(v["ms_runs"]))
     return out
 
 

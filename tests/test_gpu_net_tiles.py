@@ -1,0 +1,241 @@
+"""The warm-start network at the tile heights its production launches use.
+
+Each convolution launch takes the tallest of 64, 32 or 16 output rows per CTA that still gives
+the grid four waves.  The small network tests select 16 rows; the volumes here select 64 rows
+(8 x 1024 x 640, as the 120 x 1080 x 1920 inference does) and 32 rows (32 x 256 x 512, the
+profiled case).  Every layer alone is compared with the FP64 oracle's plain convolution loops on
+the GPU layer's own bf16 input, so that only the fp32 accumulation and the final bf16 rounding
+differ: |gpu - ref| <= 2^-8 |ref| + 1e-5 sum|w x| (bf16's unit roundoff on the stored output,
+and an fp32-accumulation bound relative to the sum of the absolute products).  The sampled
+voxels include the tile seams along h and w, the rows where the accumulator ring in tensor
+memory wraps (every 16 rows of a tile for 32 output channels, every 32 for 16) and the volume's
+faces.  The data gradient (flipped taps, ReLU mask) is checked the same way, the weight gradient
+over a whole smaller volume, and the whole network at sampled voxels on the 9 x 9 x 9 crop
+around each (one voxel's output depends on nothing else).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2212_08058_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+C_IN = 9          # 8 feature channels and the coarse start, as the trained network
+EPS_ACC = 1e-5    # fp32 accumulation, relative to sum |w x|
+U_BF16 = 2.0 ** -8
+
+
+@pytest.fixture(scope="module")
+def sf():
+    from paper_2212_08058_gb300 import build, sfseg
+    build.build()
+    oracle.build()
+    return sfseg
+
+
+def _tile_rows(T, H, W):
+    """The row count per CTA the convolution launch picks for this volume (see net.cu)."""
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    for hr in (64, 32, 16):
+        if T * -(-W // 128) * -(-H // hr) >= 4 * nsm:
+            return hr
+    return 16
+
+
+def _points(T, H, W, HR, seed, n_random=40):
+    hs = {0, 1, H - 2, H - 1}
+    for base in (HR, 2 * HR, (H // HR - 1) * HR):      # tile seams along h
+        hs.update({base - 1, base, base + 1})
+    for j in (15, 16, 17, 31, 32, 33):                   # ring wraps inside the second tile
+        hs.add(HR + j)
+    ws = {0, 1, 126, 127, 128, 129, 255, 256, W - 129, W - 128, W - 2, W - 1}
+    pts = set()
+    for h in hs:
+        for t in (0, T // 2, T - 1):
+            for w in (0, 127, 128, W - 1):
+                pts.add((t, h, w))
+    for w in ws:
+        for t in (0, T - 1):
+            for h in (0, HR - 1, HR, H - 1):
+                pts.add((t, h, w))
+    rng = np.random.default_rng(seed)
+    for _ in range(n_random):
+        pts.add(tuple(int(v) for v in rng.integers((0, 0, 0), (T, H, W))))
+    return sorted(p for p in pts if 0 <= p[0] < T and 0 <= p[1] < H and 0 <= p[2] < W)
+
+
+def _crop(a, p, r, shape):
+    """a[t-r..t+r, h-r..h+r, w-r..w+r] clipped to the volume (zero padding is the oracle's) as
+    float64, and the index of p inside it."""
+    sl = tuple(slice(max(c - r, 0), min(c + r + 1, n)) for c, n in zip(p, shape))
+    return a[sl].float().cpu().numpy().astype(np.float64), tuple(c - s.start for c, s in zip(p, sl))
+
+
+def _bf16(a):
+    return synth.to_bf16_round(np.asarray(a, dtype=np.float32)).astype(np.float64)
+
+
+def _layer_params(net):
+    return [(_bf16(w), b.astype(np.float64)) for w, b in net.unflatten(net.get_params())]
+
+
+def _check_fwd(layer, x_in, out, params, pts, shape):
+    wt, b = params[layer]
+    cin = wt.shape[-1]
+    worst = 0.0
+    for p in pts:
+        xc, ci = _crop(x_in, p, 1, shape)
+        xc = xc[..., :cin]
+        ref = oracle.conv3d_fwd(xc, wt, b)[ci]
+        S = oracle.conv3d_fwd(np.abs(xc), np.abs(wt), np.abs(b))[ci]
+        if layer < 3:
+            ref = np.maximum(ref, 0.0)
+            got = out[p].float().cpu().numpy().astype(np.float64)
+        else:
+            ref = ref[:1]
+            got = np.array([float(out[p])])
+            S = S[:1]
+        err = np.abs(got - ref)
+        tol = U_BF16 * np.abs(ref) + EPS_ACC * S if layer < 3 else EPS_ACC * S
+        assert np.all(err <= tol), (layer, p, float((err / np.maximum(tol, 1e-30)).max()))
+        worst = max(worst, float((err / np.maximum(S, 1e-30)).max()))
+    return worst
+
+
+def _forward_layers(net, x16):
+    a1 = net.layer_forward(0, x16)
+    a2 = net.layer_forward(1, a1)
+    a3 = net.layer_forward(2, a2)
+    z, x0 = net.layer_forward(3, a3)
+    net.check()
+    return [x16, a1, a2, a3], z, x0
+
+
+def _input16(T, H, W, seed):
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    x = torch.zeros((T, H, W, 16), device="cuda", dtype=torch.bfloat16)
+    x[..., :C_IN] = torch.rand((T, H, W, C_IN), device="cuda", generator=gen).to(torch.bfloat16)
+    return x
+
+
+@pytest.mark.parametrize("shape,hr", [((8, 1024, 640), 64), ((32, 256, 512), 32)], ids=["rows64", "rows32"])
+def test_layers_at_production_tile_heights(sf, shape, hr):
+    """Each layer's output at sampled voxels against the oracle's convolution of the GPU layer's
+    own input, at the tile height the launch picks for this volume."""
+    T, H, W = shape
+    assert _tile_rows(T, H, W) == hr
+    net = sf.WarmStartNet(C_IN, seed=11)
+    params = _layer_params(net)
+    x16 = _input16(T, H, W, 900 + hr)
+    ins, z, x0 = _forward_layers(net, x16)
+    pts = _points(T, H, W, hr, seed=hr)
+    outs = [ins[1], ins[2], ins[3], z]
+    for layer in range(4):
+        _check_fwd(layer, ins[layer], outs[layer], params, pts, shape)
+    # the softplus epilogue of the last layer
+    zz = z.double()
+    sp = torch.where(zz > 20, zz, torch.log1p(torch.exp(zz)))
+    assert float(((x0.double() - sp).abs() / sp).max()) <= 1e-5
+    net.close()
+
+
+@pytest.mark.parametrize("shape,hr", [((8, 1024, 640), 64), ((32, 256, 512), 32)], ids=["rows64", "rows32"])
+def test_data_gradient_at_production_tile_heights(sf, shape, hr):
+    """dx = conv^T(dz) * [x > 0] of layers 1..3 (the data-gradient convolution on the tensor
+    cores) at sampled voxels against the oracle's reverse loops on the same bf16 inputs."""
+    T, H, W = shape
+    assert _tile_rows(T, H, W) == hr
+    net = sf.WarmStartNet(C_IN, seed=12)
+    params = _layer_params(net)
+    ins, _, _ = _forward_layers(net, _input16(T, H, W, 910 + hr))
+    gen = torch.Generator(device="cuda").manual_seed(920 + hr)
+    pts = _points(T, H, W, hr, seed=100 + hr, n_random=25)
+    for layer in (1, 2, 3):
+        x = ins[layer]
+        if layer == 3:
+            dz = torch.zeros((T, H, W, 16), device="cuda", dtype=torch.bfloat16)
+            dz[..., 0] = torch.randn((T, H, W), device="cuda", generator=gen).to(torch.bfloat16)
+        else:
+            dz = torch.randn((T, H, W, 32), device="cuda", generator=gen).to(torch.bfloat16)
+        dx, _, _ = net.layer_backward(layer, x, dz)
+        net.check()
+        wt, _ = params[layer]
+        cout = wt.shape[0]
+        for p in pts:
+            xc, ci = _crop(x, p, 1, shape)
+            dzc, _ = _crop(dz, p, 1, shape)
+            dzc = dzc[..., :cout]
+            dxr, _, _ = oracle.conv3d_bwd(xc, wt, dzc)
+            Sx, _, _ = oracle.conv3d_bwd(np.abs(xc), np.abs(wt), np.abs(dzc))
+            ref = dxr[ci] * (xc[ci] > 0)
+            S = Sx[ci]
+            got = dx[p].float().cpu().numpy().astype(np.float64)
+            err = np.abs(got - ref)
+            tol = U_BF16 * np.abs(ref) + EPS_ACC * S
+            assert np.all(err <= tol), (layer, p, float((err / np.maximum(tol, 1e-30)).max()))
+    net.close()
+
+
+def test_weight_gradient_whole_volume(sf):
+    """dW and db of every layer over a whole 4 x 64 x 200 volume (two 128-voxel tiles along w,
+    a ragged second one) against the oracle's reverse loops, relative to the sum of the
+    absolute products of each entry."""
+    T, H, W = 4, 64, 200
+    net = sf.WarmStartNet(C_IN, seed=13)
+    params = _layer_params(net)
+    ins, _, _ = _forward_layers(net, _input16(T, H, W, 930))
+    gen = torch.Generator(device="cuda").manual_seed(931)
+    for layer in range(4):
+        x = ins[layer]
+        if layer == 3:
+            dz = torch.zeros((T, H, W, 16), device="cuda", dtype=torch.bfloat16)
+            dz[..., 0] = torch.randn((T, H, W), device="cuda", generator=gen).to(torch.bfloat16)
+        else:
+            dz = torch.randn((T, H, W, 32), device="cuda", generator=gen).to(torch.bfloat16)
+        _, dW, db = net.layer_backward(layer, x, dz, want_dx=False)
+        net.check()
+        wt, _ = params[layer]
+        cout, cin = wt.shape[0], wt.shape[-1]
+        xa = x.float().cpu().numpy().astype(np.float64)[..., :cin]
+        dza = dz.float().cpu().numpy().astype(np.float64)[..., :cout]
+        _, dwr, dbr = oracle.conv3d_bwd(xa, wt, dza, need_dx=False)
+        _, dws, dbs = oracle.conv3d_bwd(np.abs(xa), np.abs(wt), np.abs(dza), need_dx=False)
+        gw = dW.cpu().numpy().astype(np.float64)
+        gb = db.cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(gw - dwr) <= 4 * EPS_ACC * dws + 1e-30), (layer, float(np.abs(gw - dwr).max()))
+        assert np.all(np.abs(gb - dbr) <= 4 * EPS_ACC * dbs + 1e-30), (layer, float(np.abs(gb - dbr).max()))
+    net.close()
+
+
+@pytest.mark.parametrize("shape,hr", [((8, 1024, 640), 64), ((32, 256, 512), 32)], ids=["rows64", "rows32"])
+def test_network_sampled_at_production_tile_heights(sf, shape, hr):
+    """sfseg_net_forward (8 bf16 channels + the extra channel) at sampled voxels against the
+    oracle's FP64 network on the 9 x 9 x 9 crop around each voxel, within the end-to-end bf16
+    tolerance of the small network test (three hidden activations rounded to bf16)."""
+    T, H, W = shape
+    assert _tile_rows(T, H, W) == hr
+    gen = torch.Generator(device="cuda").manual_seed(940 + hr)
+    feats = torch.rand((8, T, H, W), device="cuda", generator=gen).to(torch.bfloat16)
+    extra = torch.rand((T, H, W), device="cuda", generator=gen)
+    net = sf.WarmStartNet(C_IN, seed=14)
+    params = _layer_params(net)
+    x0 = net.forward(feats, extra)
+    net.check()
+    extra_b = extra.to(torch.bfloat16)
+    pts = _points(T, H, W, hr, seed=200 + hr, n_random=10)[::3]
+    refs, gots = [], []
+    for p in pts:
+        sl = tuple(slice(max(c - 4, 0), min(c + 5, n)) for c, n in zip(p, shape))
+        fc = feats[(slice(None),) + sl].float().cpu().numpy().astype(np.float64)
+        ec = extra_b[sl].float().cpu().numpy().astype(np.float64)
+        crop = np.concatenate([fc, ec[None]], axis=0)
+        ref, _ = oracle.warmstart_forward(crop, params)
+        ci = tuple(c - s.start for c, s in zip(p, sl))
+        refs.append(ref[ci])
+        gots.append(float(x0[p]))
+    refs, gots = np.array(refs), np.array(gots)
+    assert np.all(gots > 0)
+    assert np.abs(gots - refs).max() <= 3e-2 * np.abs(refs).max(), float(np.abs(gots - refs).max())
+    net.close()

@@ -3,8 +3,9 @@ memory (a fixed memory budget reserved at start-up, latency-bound loops where cu
 synchronise the device, plug-ins without a long-lived workspace).
 
 Called through the C ABI several times in a row, it must give what the handle-based
-sfseg_power_iterate gives (same kernels, tolerance of the forward parity tests), leave no stale
-state behind between calls that share its scratch, and not change the device's free memory.
+sfseg_power_iterate gives (same kernels, tolerance of the forward parity tests), match the FP64
+oracle directly (float32 and bf16 features), leave no stale state behind between calls that
+share its scratch, and not change the device's free memory.
 This file is collected last so that a failure here does not hide any other test.
 """
 import ctypes
@@ -13,6 +14,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2212_08058_gb300 import synth
 
 pytestmark = pytest.mark.gpu
@@ -24,6 +26,7 @@ TOL_F32 = 1e-5
 def sf():
     from paper_2212_08058_gb300 import build, sfseg
     build.build()
+    oracle.build()
     return sfseg
 
 
@@ -32,17 +35,20 @@ def _call(sf, feats, x, weights, radius, iters, init, norms, alpha=1.0, p=0.1):
     C, T, H, W = feats.shape
     nb = sf.neighborhood(radius)
     w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
+    dtype = sf.SFSEG_BF16 if feats.dtype == torch.bfloat16 else sf.SFSEG_F32
     rc = sf.lib().sfseg_power_iterate_noalloc(
-        ctypes.byref(sf.Params(alpha, p)), C, T, H, W, ctypes.c_void_p(feats.data_ptr()), sf.SFSEG_F32,
+        ctypes.byref(sf.Params(alpha, p)), C, T, H, W, ctypes.c_void_p(feats.data_ptr()), dtype,
         w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)) if w is not None else None, 0.0, ctypes.byref(nb),
         iters, ctypes.c_void_p(x.data_ptr()), sf.INIT[init], norms.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert rc == 0, sf.lib().sfseg_last_error().decode()
 
 
-def _noalloc(sf, V, weights, radius, iters, init):
+def _noalloc(sf, V, weights, radius, iters, init, bf16=False):
     C, T, H, W = V.shape
     feats = torch.from_numpy(np.ascontiguousarray(V)).cuda()
+    if bf16:
+        feats = feats.to(torch.bfloat16)
     x = torch.empty((T, H, W), device="cuda")
     norms = np.empty(max(iters, 1))
     _call(sf, feats, x, weights, radius, iters, init, norms)
@@ -50,12 +56,14 @@ def _noalloc(sf, V, weights, radius, iters, init):
     return x.cpu().numpy(), norms[:iters]
 
 
-def _handle(sf, V, weights, radius, iters, init, x0=None):
+def _handle(sf, V, weights, radius, iters, init, x0=None, bf16=False):
     C, T, H, W = V.shape
     with sf.PowerIteration(C, T, H, W) as h:
         x = None if x0 is None else torch.from_numpy(np.ascontiguousarray(x0, dtype=np.float32)).cuda()
-        x, nu = h.power_iterate(torch.from_numpy(np.ascontiguousarray(V)).cuda(), weights, 0.0, radius,
-                                iters=iters, x=x, init=init, return_norms=True)
+        feats = torch.from_numpy(np.ascontiguousarray(V)).cuda()
+        if bf16:
+            feats = feats.to(torch.bfloat16)
+        x, nu = h.power_iterate(feats, weights, 0.0, radius, iters=iters, x=x, init=init, return_norms=True)
         torch.cuda.synchronize()
         return x.cpu().numpy(), nu
 
@@ -73,6 +81,33 @@ def test_noalloc_matches_handle_on_consecutive_calls(sf):
         xh, nuh = _handle(sf, V, w, r, K, init)
         assert np.abs(xn.astype(np.float64) - xh.astype(np.float64)).max() <= TOL_F32
         np.testing.assert_allclose(nun, nuh, rtol=1e-5)
+
+
+def _oracle(V, weights, radius, iters, init, p=0.1, alpha=1.0):
+    """The FP64 oracle on the same (already rounded) features: Eq. 9, then Eq. 7 + Eq. 8."""
+    V = np.asarray(V, dtype=np.float64)
+    f = oracle.combine(V, weights) if V.shape[0] > 1 else V[0]
+    x0 = f if init == "smap" else np.ones(f.shape)
+    return oracle.power_filter(f, f, p, alpha, radius, x0, iters)
+
+
+@pytest.mark.parametrize("bf16", [False, True], ids=["f32_features", "bf16_features"])
+def test_noalloc_matches_oracle(sf, bf16):
+    """One call per feature type against the FP64 oracle (iterate parity at equal iteration
+    count, 1e-5 max-abs on the unit-norm x, the forward tests' tolerance), and against the handle
+    path with the same features.  bf16 features are widened exactly on both sides; the iterate
+    storage stays float32."""
+    cases = [(synth.drifting_blob(8, 64, 64, seed=1000), None, (1, 3, 3), 20, "uniform")]
+    V3, _, w3 = synth.multichannel(6, 48, 80, C=3, seed=3005)
+    cases.append((V3, w3 * 4.0, (2, 7, 7), 12, "smap"))
+    for V, w, r, K, init in cases:
+        Vr = synth.to_bf16_round(V) if bf16 else V
+        xn, nun = _noalloc(sf, V, w, r, K, init, bf16=bf16)
+        xo, nuo = _oracle(Vr, w, r, K, init)
+        assert np.abs(xn.astype(np.float64) - xo).max() <= TOL_F32
+        np.testing.assert_allclose(nun, nuo, rtol=1e-5)
+        xh, _ = _handle(sf, V, w, r, K, init, bf16=bf16)
+        assert np.abs(xn.astype(np.float64) - xh.astype(np.float64)).max() <= TOL_F32
 
 
 def test_noalloc_takes_no_device_memory(sf):
