@@ -574,6 +574,61 @@ def bench_time_to_residual(sfseg, synth, warmstart, tol: float = 1e-4, repeats: 
     return res
 
 
+def bench_net_training(sfseg, synth, steps: int = 20):
+    """The warm-start network's training step (forward, cosine loss, data and weight gradients,
+    AdamW) on one 16 x 128 x 128 training volume (8 channels + the coarse start), and its weight-
+    gradient kernel alone (tcgen05, one 32 -> 32 layer) at 32 x 256 x 512 with the forward
+    convolution of the same layer beside it; CUDA events.  Algorithmic flops: 2 x 27 x C_in x
+    C_out per voxel for each convolution and each weight gradient."""
+    import torch
+    C, T, H, W = 8, 16, 128, 128
+    V = synth.training_volume_torch(7000, T, H, W, C).to(torch.bfloat16)
+    extra = torch.rand((T, H, W), device="cuda")
+    target = torch.rand((T, H, W), device="cuda")
+    net = sfseg.WarmStartNet(C + 1, seed=3)
+    for _ in range(3):
+        net.backward(V, target, extra=extra)
+        net.adamw(lr=1e-4)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        net.backward(V, target, extra=extra)
+        net.adamw(lr=1e-4)
+    e1.record()
+    torch.cuda.synchronize()
+    step_ms = e0.elapsed_time(e1) / steps
+    nvox = T * H * W
+    fwd = 2 * 27 * (9 * 32 + 32 * 32 + 32 * 32 + 32 * 1)
+    dgrad = 2 * 27 * (1 * 32 + 32 * 32 + 32 * 32)
+    wgr = fwd
+    out = {"training_step": {"volume": f"C={C}+1 bf16 {T}x{H}x{W}", "ms": step_ms,
+                             "algorithmic_tflops": (fwd + dgrad + wgr) * nvox / (step_ms * 1e-3) / 1e12,
+                             "note": "synchronises once per step (loss read-back)"}}
+    Tb, Hb, Wb = 32, 256, 512
+    gen = torch.Generator(device="cuda").manual_seed(7001)
+    x = torch.rand((Tb, Hb, Wb, 32), device="cuda", generator=gen).to(torch.bfloat16)
+    dz = torch.randn((Tb, Hb, Wb, 32), device="cuda", generator=gen).to(torch.bfloat16)
+    for name, fn in (("weight_gradient", lambda: net.layer_backward(1, x, dz, want_dx=False)),
+                     ("forward_conv", lambda: net.layer_forward(1, x)),
+                     ("data_gradient_and_weight_gradient", lambda: net.layer_backward(1, x, dz, want_dx=True))):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(10):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        fl = 2 * 27 * 32 * 32 * Tb * Hb * Wb * (2 if name.startswith("data") else 1)
+        out[name] = {"volume": f"{Tb}x{Hb}x{Wb}, 32 -> 32 channels", "ms": ms,
+                     "algorithmic_tflops": fl / (ms * 1e-3) / 1e12}
+    net.check()
+    net.close()
+    return out
+
+
 EXTRAS = {
     "bf16_multichannel": lambda sf, sy: bench_bf16_multichannel(sf, sy),
     "soft_binarize": lambda sf, sy: bench_soft_binarize(sf, sy),
@@ -584,6 +639,7 @@ EXTRAS = {
     "r133_storage": lambda sf, sy: bench_r133_storage(sf, sy, steps=2),
     "exact_kernel": lambda sf, sy: bench_exact_kernel(sf, sy),
     "time_to_residual": lambda sf, sy, ws: bench_time_to_residual(sf, sy, ws),
+    "net_training": lambda sf, sy: bench_net_training(sf, sy),
 }
 
 
@@ -738,6 +794,7 @@ def main():
             out["r133_storage"] = bench_r133_storage(sfseg, synth)
             out["exact_kernel"] = bench_exact_kernel(sfseg, synth)
             out["time_to_residual"] = bench_time_to_residual(sfseg, synth, warmstart)
+            out["net_training"] = bench_net_training(sfseg, synth)
         if world == 1 and not args.no_cpu_baseline:
             out["cpu_baseline"], x_oracle, k = cpu_baseline()
             # the error of the timed result: the GPU iterate after the oracle's iteration count,

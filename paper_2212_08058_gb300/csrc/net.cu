@@ -394,6 +394,207 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
 }
 
+// ------------------------------------------------------------------ weight gradient (tcgen05)
+// dW[co][tap][ci] = sum_v dz[v][co] x[v + tap][ci] and db[co] = sum_v dz[v][co] as GEMMs with the
+// voxels as the reduction dimension K.  A work unit is (x frame t, dz row h, a 128-voxel segment
+// along w).  With the x frame fixed, the taps (dt, dh, dw) of one unit form three products, one
+// per dw:
+//   D_dw[(j, ci), (s, co)] += sum_k x[t, h - 1 + j, w0 + k + dw - 1, ci] * dz[t - 1 + s, h, w0 + k, co]
+// for j = dh + 1 in 0..2 and s = 1 - dt in 0..2: M = 128 stacks four 32-channel row blocks of x
+// (the fourth is a constant 1, so its rows of D sum dz: the bias gradient), N stacks the three dz
+// frames (3 x 32 channels; 3 x 16 for the last layer's one channel padded to 16).  Both operands
+// are read in the MN-major layout straight from the TMA copies of the channels-last activations:
+// [block][8-channel chunk][voxels][8 channels], where a core matrix is 8 voxels (K) x 8 channels
+// (16 bytes) and a shift by one voxel along w is a 16-byte offset of the descriptor's start.
+// Every unit of a CTA accumulates into the same TMEM columns; at the end the CTA writes its
+// partial sums to a scratch slice and a second kernel adds the slices in a fixed order.
+constexpr int WG_XV = MT + 2;                              // x voxels per row (w halo 1)
+constexpr int WG_CHA = (WG_XV * 16 + 127) / 128 * 128;     // A chunk stride (2176 B)
+constexpr int WG_CHB = MT * 16;                            // B chunk stride (2048 B)
+constexpr int WG_A_BYTES = 16 * WG_CHA;                    // 4 row blocks x 4 chunks
+constexpr int WG_NS = 3;                                   // stages
+
+template <int NCI, int NCO>
+struct WgCfg {
+    static constexpr int N = 3 * NCO * 8;                  // 96 or 48
+    static constexpr int B_BYTES = 3 * NCO * WG_CHB;
+    static constexpr int STAGE = WG_A_BYTES + B_BYTES;
+    static constexpr int TMEM_COLS = 3 * N <= 256 ? 256 : 512;
+    static constexpr int SMEM = WG_NS * STAGE + (2 * WG_NS + 2) * 8 + 16 + 128;
+    static constexpr int PART = 3 * N * 128;               // floats of one CTA's partial sums
+};
+
+struct WgArgs {
+    int T, H, W, nws, units, per;   // per: units of each CTA (the last may have fewer, none has 0)
+    float* part;     // [gridDim.x][3 dw][N][128 m]
+    int* flags;
+};
+
+// Instruction descriptor, kind::f16: bf16 A and B, both MN-major, fp32 D, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int n) { return idesc_bf16(n) | (1u << 15) | (1u << 16); }
+
+template <int NCI, int NCO>
+__global__ void __launch_bounds__(NTHR, 1)
+wgrad_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUtensorMap dzmap, WgArgs a) {
+    using C = WgCfg<NCI, NCO>;
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    unsigned char* sm = (unsigned char*)(((uintptr_t)sm_raw + 127) & ~(uintptr_t)127);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + WG_NS * C::STAGE);
+    uint64_t* full = bar;               // [WG_NS]
+    uint64_t* empty = bar + WG_NS;      // [WG_NS]
+    uint64_t* done = bar + 2 * WG_NS;   // every MMA of the CTA has completed
+    uint64_t* drain = done + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 2 * WG_NS + 2);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // this CTA's contiguous range of units
+    const int u0 = blockIdx.x * a.per, u1 = min(a.units, u0 + a.per);
+    const int nu = max(u1 - u0, 0);
+
+    // the constant row block (ones) of every stage, and the channel chunks an input with fewer
+    // than 32 channels (NCI < 4) does not fill (zeros); no copy ever writes either
+    for (int i = threadIdx.x; i < WG_NS * 16 * WG_CHA / 16; i += blockDim.x) {
+        const int st = i / (16 * WG_CHA / 16), r = i % (16 * WG_CHA / 16);
+        const int blk = r / (WG_CHA / 16);          // (j, c) block: j = blk / 4, c = blk % 4
+        uint4* p = reinterpret_cast<uint4*>(sm + st * C::STAGE) + r;
+        if (blk >= 12) *p = make_uint4(0x3F803F80u, 0x3F803F80u, 0x3F803F80u, 0x3F803F80u);   // bf16 1.0 x 8
+        else if (blk % 4 >= NCI) *p = make_uint4(0u, 0u, 0u, 0u);
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < WG_NS; ++i) {
+            mb_init(&full[i], 1);
+            mb_init(&empty[i], 1);
+        }
+        mb_init(done, 1);
+        mb_init(drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(C::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    int issued = 0;
+    bool mma_ok = true;
+    if (warp == 0) {
+        if (lane == 0) {   // ---------------- producer
+            for (int i = 0; i < nu; ++i) {
+                const int s = i % WG_NS;
+                if (i >= WG_NS && !mb_wait(&empty[s], (uint32_t)((i / WG_NS - 1) & 1), a.flags)) break;
+                issued = i + 1;
+                int u = u0 + i;
+                const int ws = u % a.nws;
+                u /= a.nws;
+                const int h = u % a.H, t = u / a.H;
+                const int w0 = ws * MT;
+                unsigned char* st = sm + s * C::STAGE;
+                mb_expect(&full[s], 3u * NCI * (uint32_t)(WG_XV * 16) + 3u * NCO * (uint32_t)WG_CHB);
+                for (int j = 0; j < 3; ++j)
+                    for (int c = 0; c < NCI; ++c)
+                        tma4(st + (j * 4 + c) * WG_CHA, &xmap, &full[s], 8 * c, w0 - 1, h - 1 + j, t);
+                for (int f = 0; f < 3; ++f)
+                    for (int c = 0; c < NCO; ++c)
+                        tma4(st + WG_A_BYTES + (f * NCO + c) * WG_CHB, &dzmap, &full[s], 8 * c, w0, h, t - 1 + f);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // ---------------- MMA issuer
+            const uint32_t base = su32(sm);
+            constexpr uint32_t ID = idesc_bf16_mn(C::N);
+            for (int i = 0; i < nu; ++i) {
+                const int s = i % WG_NS;
+                if (!mb_wait(&full[s], (uint32_t)((i / WG_NS) & 1), a.flags)) {
+                    mma_ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sa = base + (uint32_t)(s * C::STAGE), sb = sa + WG_A_BYTES;
+#pragma unroll
+                for (int dw = 0; dw < 3; ++dw)
+#pragma unroll
+                    for (int kk = 0; kk < MT / 16; ++kk) {
+                        const uint64_t ad = sdesc(sa + (uint32_t)((kk * 16 + dw) * 16), WG_CHA, 128);
+                        const uint64_t bd = sdesc(sb + (uint32_t)(kk * 16 * 16), WG_CHB, 128);
+                        umma(tmem + (uint32_t)(dw * C::N), ad, bd, ID, (i > 0 || kk > 0) ? 1u : 0u);
+                    }
+                umma_commit(&empty[s]);
+            }
+            umma_commit(done);   // arrives when all of this thread's MMAs have completed
+        }
+    } else {   // ---------------- epilogue: warps 2..5 write the partial sums
+        const int q = warp & 3;
+        const bool ok = mb_wait(done, 0, a.flags);
+        tc_fence_after();
+        if (ok && nu > 0) {
+            float* out = a.part + (size_t)blockIdx.x * C::PART;
+            const int m = q * 32 + lane;
+#pragma unroll 1
+            for (int c0 = 0; c0 < 3 * C::N; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld<16>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+                tmem_ld_wait();
+#pragma unroll
+                for (int e = 0; e < 16; ++e) out[(size_t)(c0 + e) * 128 + m] = __uint_as_float(r[e]);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (*reinterpret_cast<volatile int*>(a.flags) & kFlagTimeout) {
+        // a bounded wait gave up: let the copies and MMAs this CTA issued land before its shared
+        // memory and tensor memory are released (each wait bounded)
+        if (warp == 0 && lane == 0) {
+            for (int s = 0; s < WG_NS && s < issued; ++s) {
+                const int last = s + ((issued - 1 - s) / WG_NS) * WG_NS;
+                mb_settle(&full[s], (uint32_t)((last / WG_NS) & 1));
+            }
+        } else if (warp == 1 && lane == 0) {
+            umma_commit(drain);
+            mb_settle(drain, 0);
+        }
+        __syncthreads();
+    }
+    (void)mma_ok;
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
+}
+
+// Sum of the CTAs' partial sums in a fixed order: dW[co][tap][ci] with tap = 9 (dt + 1) +
+// 3 (dh + 1) + (dw + 1) from row block j = dh + 1, dz frame s = 1 - dt; db[co] from the constant
+// row block (m = 96) of the dz frame s = 1 (the others repeat it).
+template <int NCI, int NCO>
+__global__ void wgrad_reduce(const float* part, int nparts, int cout, int cin, float* dW, float* db) {
+    using C = WgCfg<NCI, NCO>;
+    const int total = cout * 27 * cin;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < total + cout; idx += gridDim.x * blockDim.x) {
+        int n, m, dw;
+        if (idx < total) {
+            const int ci = idx % cin, tap = (idx / cin) % 27, co = idx / (cin * 27);
+            const int dtp = tap / 9, dhp = (tap / 3) % 3;
+            dw = tap % 3;
+            n = (2 - dtp) * NCO * 8 + co;
+            m = dhp * 32 + ci;
+        } else {
+            const int co = idx - total;
+            dw = 1;
+            n = NCO * 8 + co;
+            m = 96;
+        }
+        double acc = 0.0;
+        for (int p = 0; p < nparts; ++p) acc += (double)part[(size_t)p * C::PART + ((size_t)dw * C::N + n) * 128 + m];
+        if (idx < total) dW[idx] = (float)acc;
+        else db[idx - total] = (float)acc;
+    }
+}
+
 // ------------------------------------------------------------------------ small kernels
 // Caller's channels [C][T][H][W] (float or bf16), plus an optional float [T][H][W] channel after
 // them -> bf16 [T][H][W][16], remaining channels zero.
@@ -440,48 +641,6 @@ __global__ void pack_weights(const float* W, int cout, int cin, int COUTP, int C
         }
         out[idx] = __float2bfloat16_rn(v);
     }
-}
-
-// Weight gradient on the CUDA cores: dW[co][tap][ci] += sum_v dz[v][co] * x[v + tap][ci],
-// db[co] += sum_v dz[v][co].  dz: bf16 [N][dzc], x: bf16 [N][xc]; grid (27, splits).
-__global__ void wgrad_kernel(const __nv_bfloat16* dz, int dzc, int cout, const __nv_bfloat16* x, int xc, int cin, int T,
-                             int H, int W, float* dW, float* db) {
-    const int tap = blockIdx.x;
-    const int dt = tap / 9 - 1, dh = (tap / 3) % 3 - 1, dw = tap % 3 - 1;
-    const int64_t N = (int64_t)T * H * W;
-    const int nsplit = gridDim.y;
-    const int64_t per = (N + nsplit - 1) / nsplit;
-    const int64_t v0 = blockIdx.y * per, v1 = min(N, v0 + per);
-    __shared__ float sdz[64][33];
-    __shared__ float sx[64][33];
-    const int co = threadIdx.x / 32, ci = threadIdx.x % 32;   // 1024 threads: (co, ci)
-    float acc = 0.f, accb = 0.f;
-    for (int64_t base = v0; base < v1; base += 64) {
-        for (int i = threadIdx.x; i < 64 * 32; i += blockDim.x) {
-            const int vv = i / 32, c = i % 32;
-            const int64_t v = base + vv;
-            float a = 0.f, bx = 0.f;
-            if (v < v1) {
-                if (c < cout) a = __bfloat162float(dz[v * dzc + c]);
-                const int64_t t = v / ((int64_t)H * W), rem = v % ((int64_t)H * W);
-                const int h = (int)(rem / W), w = (int)(rem % W);
-                const int tt = (int)t + dt, hh = h + dh, ww = w + dw;
-                if (c < cin && tt >= 0 && tt < T && hh >= 0 && hh < H && ww >= 0 && ww < W)
-                    bx = __bfloat162float(x[(((int64_t)tt * H + hh) * W + ww) * xc + c]);
-            }
-            sdz[vv][c] = a;
-            sx[vv][c] = bx;
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int vv = 0; vv < 64; ++vv) {
-            acc = fmaf(sdz[vv][co], sx[vv][ci], acc);
-            accb += sdz[vv][co];
-        }
-        __syncthreads();
-    }
-    if (co < cout && ci < cin) atomicAdd(&dW[((int64_t)co * 27 + tap) * cin + ci], acc);
-    if (tap == 0 && ci == 0 && co < cout) atomicAdd(&db[co], accb);
 }
 
 // Cosine-loss pieces: sums of x*g, x*x, g*g (FP64 via block sums).
@@ -575,6 +734,20 @@ bool act_map(CUtensorMap* m, const void* base, int C, int T, int H, int W) {
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// 4D map over a channels-last bf16 activation [T][H][W][C] with a box of 8 channels x bw voxels
+// x 1 row x 1 frame (one chunk of one row).
+bool row_map(CUtensorMap* m, const void* base, int C, int T, int H, int W, int bw) {
+    EncodeFn fn = encode();
+    if (!fn) return false;
+    cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)T};
+    cuuint64_t str[3] = {(cuuint64_t)C * 2, (cuuint64_t)C * 2 * W, (cuuint64_t)C * 2 * W * H};
+    cuuint32_t box[4] = {8, (cuuint32_t)bw, 1, 1};
+    cuuint32_t es[4] = {1, 1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, str, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int blocks_for(int64_t n, int per = 256) {
     int64_t b = (n + per - 1) / per;
     const int cap = 16 * num_sms();
@@ -596,6 +769,7 @@ struct sfseg_net {
     __nv_bfloat16 *x16 = nullptr, *a1 = nullptr, *a2 = nullptr, *a3 = nullptr, *dz16 = nullptr, *dza = nullptr,
                   *dzb = nullptr;
     float *z4 = nullptr, *x0 = nullptr;
+    float* wg_part = nullptr;   // per-CTA partial sums of the weight-gradient kernel
     double* acc = nullptr;
     int* flags = nullptr;
     bool have_fwd = false;
@@ -729,23 +903,49 @@ int net_forward(sfseg_net* n, const void* feats, int dtype, int C, const float* 
     return SFSEG_OK;
 }
 
-// dW (float32 [cout][27][cin]) and db (float32 [cout]) of layer l accumulated from dz (bf16
-// [N][dzc]) and the layer's input x (bf16 [N][xc]).
-int wgrad_into(int l, int cin, const __nv_bfloat16* dz, int dzc, const __nv_bfloat16* x, int xc, int T, int H, int W,
-               float* dW, float* db, cudaStream_t s) {
-    const int64_t N = (int64_t)T * H * W;
-    int splits = (int)((N + 4095) / 4096);
-    if (splits > 24) splits = 24;
-    if (splits < 1) splits = 1;
-    wgrad_kernel<<<dim3(27, splits), 1024, 0, s>>>(dz, dzc, kCout[l], x, xc, cin, T, H, W, dW, db);
-    count_launches(1);
+template <int NCI, int NCO>
+int run_wgrad(sfseg_net* n, int cout, int cin, const __nv_bfloat16* dz, const __nv_bfloat16* x, int T, int H, int W,
+              float* dW, float* db, cudaStream_t s) {
+    using Cf = WgCfg<NCI, NCO>;
+    CUtensorMap xm, dm;
+    if (!row_map(&xm, x, NCI * 8, T, H, W, WG_XV) || !row_map(&dm, dz, NCO * 8, T, H, W, MT))
+        return nfail(SFSEG_ERR_CUDA, "tensor map encoding failed");
+    if (!n->wg_part) NET_CUDA(cudaMalloc(&n->wg_part, (size_t)num_sms() * WgCfg<4, 4>::PART * sizeof(float)));
+    auto k = wgrad_tc<NCI, NCO>;
+    static bool attr = false;
+    if (!attr) {
+        NET_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM));
+        attr = true;
+    }
+    WgArgs a;
+    a.T = T; a.H = H; a.W = W;
+    a.nws = (W + MT - 1) / MT;
+    a.units = T * H * a.nws;
+    a.part = n->wg_part;
+    a.flags = n->flags;
+    a.per = (a.units + num_sms() - 1) / num_sms();
+    const int grid = (a.units + a.per - 1) / a.per;   // every CTA gets at least one unit
+    k<<<grid, NTHR, Cf::SMEM, s>>>(xm, dm, a);
+    wgrad_reduce<NCI, NCO><<<(cout * 27 * cin + cout + 255) / 256, 256, 0, s>>>(n->wg_part, grid, cout, cin, dW, db);
+    count_launches(2);
     NET_CUDA(cudaGetLastError());
     return SFSEG_OK;
 }
 
+// dW (float32 [cout][27][cin], overwritten) and db (float32 [cout], overwritten) of layer l from
+// dz (bf16 [N][dzc]) and the layer's input x (bf16 [N][xc]), on the tensor cores.
+int wgrad_into(sfseg_net* n, int l, int cin, const __nv_bfloat16* dz, int dzc, const __nv_bfloat16* x, int xc, int T,
+               int H, int W, float* dW, float* db, cudaStream_t s) {
+    if (xc == 16 && dzc == 32) return run_wgrad<2, 4>(n, kCout[l], cin, dz, x, T, H, W, dW, db, s);
+    if (xc == 32 && dzc == 32) return run_wgrad<4, 4>(n, kCout[l], cin, dz, x, T, H, W, dW, db, s);
+    if (xc == 32 && dzc == 16) return run_wgrad<4, 2>(n, kCout[l], cin, dz, x, T, H, W, dW, db, s);
+    return nfail(SFSEG_ERR_UNSUPPORTED, "weight gradient: unsupported channel counts");
+}
+
 int wgrad(sfseg_net* n, int l, const __nv_bfloat16* dz, int dzc, const __nv_bfloat16* x, int xc, int T, int H, int W,
           cudaStream_t s) {
-    return wgrad_into(l, layer_cin(n, l), dz, dzc, x, xc, T, H, W, n->g + n->off[2 * l], n->g + n->off[2 * l + 1], s);
+    return wgrad_into(n, l, layer_cin(n, l), dz, dzc, x, xc, T, H, W, n->g + n->off[2 * l], n->g + n->off[2 * l + 1],
+                      s);
 }
 
 uint64_t splitmix(uint64_t& x) {
@@ -823,7 +1023,7 @@ int sfseg_net_destroy(sfseg_net* n) {
     for (int l = 0; l < 4; ++l) { cudaFree(n->wf[l]); cudaFree(n->wb[l]); }
     cudaFree(n->x16); cudaFree(n->a1); cudaFree(n->a2); cudaFree(n->a3);
     cudaFree(n->dz16); cudaFree(n->dza); cudaFree(n->dzb); cudaFree(n->z4); cudaFree(n->x0);
-    cudaFree(n->acc); cudaFree(n->flags);
+    cudaFree(n->wg_part); cudaFree(n->acc); cudaFree(n->flags);
     delete n;
     return SFSEG_OK;
 }
@@ -926,9 +1126,7 @@ int sfseg_net_layer_backward(sfseg_net* n, int layer, const void* in, const void
     const int cin = layer_cin(n, layer), cinp = layer == 0 ? 16 : 32, dzc = layer == 3 ? 16 : 32;
     const __nv_bfloat16* x = (const __nv_bfloat16*)in;
     const __nv_bfloat16* g = (const __nv_bfloat16*)dz;
-    NET_CUDA(cudaMemsetAsync(dW_out, 0, (size_t)kCout[layer] * 27 * cin * sizeof(float), s));
-    NET_CUDA(cudaMemsetAsync(db_out, 0, (size_t)kCout[layer] * sizeof(float), s));
-    if (int rc = wgrad_into(layer, cin, g, dzc, x, cinp, T, H, W, dW_out, db_out, s)) return rc;
+    if (int rc = wgrad_into(n, layer, cin, g, dzc, x, cinp, T, H, W, dW_out, db_out, s)) return rc;
     if (dx_out && layer > 0) {
         if (layer == 3)
             return run_conv<16, 32, EPI_MASK>(g, T, H, W, n->wb[3], nullptr, dx_out, nullptr, x, n->flags, s);

@@ -209,6 +209,28 @@ def test_weight_gradient_whole_volume(sf):
     net.close()
 
 
+def test_weight_gradient_training_volume(sf):
+    """The weight gradient of a 32 -> 32 layer over a whole 16 x 128 x 128 training volume (the
+    volumes the network is trained on: 2048 work units spread over every SM) against the
+    oracle's reverse loops."""
+    T, H, W = 16, 128, 128
+    net = sf.WarmStartNet(C_IN, seed=15)
+    params = _layer_params(net)
+    gen = torch.Generator(device="cuda").manual_seed(950)
+    x = torch.relu(torch.randn((T, H, W, 32), device="cuda", generator=gen)).to(torch.bfloat16)
+    dz = torch.randn((T, H, W, 32), device="cuda", generator=gen).to(torch.bfloat16)
+    _, dW, db = net.layer_backward(2, x, dz, want_dx=False)
+    net.check()
+    wt, _ = params[2]
+    xa = x.float().cpu().numpy().astype(np.float64)
+    dza = dz.float().cpu().numpy().astype(np.float64)
+    _, dwr, dbr = oracle.conv3d_bwd(xa, wt, dza, need_dx=False)
+    _, dws, dbs = oracle.conv3d_bwd(np.abs(xa), np.abs(wt), np.abs(dza), need_dx=False)
+    assert np.all(np.abs(dW.cpu().numpy() - dwr) <= 4 * EPS_ACC * dws), float(np.abs(dW.cpu().numpy() - dwr).max())
+    assert np.all(np.abs(db.cpu().numpy() - dbr) <= 4 * EPS_ACC * dbs), float(np.abs(db.cpu().numpy() - dbr).max())
+    net.close()
+
+
 @pytest.mark.parametrize("shape,hr", [((8, 1024, 640), 64), ((32, 256, 512), 32)], ids=["rows64", "rows32"])
 def test_network_sampled_at_production_tile_heights(sf, shape, hr):
     """sfseg_net_forward (8 bf16 channels + the extra channel) at sampled voxels against the
