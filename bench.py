@@ -564,6 +564,19 @@ def bench_time_to_residual(sfseg, synth, warmstart, tol: float = 1e-4, repeats: 
     trained = warmstart.load(net)
     res = warmstart.compare_starts(V, w, RADIUS, tol=tol, net=net if trained else None, max_iters=3000,
                                    repeats=repeats)
+    if trained:
+        # the network's forward pass alone on this volume (what its start costs)
+        extra = torch.rand((T5, H5, W5), device="cuda")
+        net.forward(V, extra)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            net.forward(V, extra)
+        e1.record()
+        torch.cuda.synchronize()
+        res["network_forward_ms"] = e0.elapsed_time(e1) / 3
+        del extra
     net.close()
     del V
     torch.cuda.empty_cache()

@@ -336,9 +336,9 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
                 float2 pa[C::NPAIR];
 #pragma unroll
                 for (int j = 0; j < C::NPAIR; ++j) pa[j] = ld_pair(qr + 2 * j);
-                float2 acc[2][4];   // even and odd taps: eight independent chains
+                float2 acc[4];   // four independent chains (one per column pair)
 #pragma unroll
-                for (int m = 0; m < 4; ++m) acc[0][m] = acc[1][m] = make_float2(0.f, 0.f);
+                for (int m = 0; m < 4; ++m) acc[m] = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int d = 0; d <= 2 * RW; ++d) {
                     const float2 gd = gwr[d];
@@ -346,17 +346,17 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
                     for (int m = 0; m < 4; ++m) {
                         const int q = 2 * m + d + C::ODD;
                         if ((q & 1) && RW <= 4) {   // odd-aligned pair: two scalar FMAs
-                            acc[d & 1][m].x = fmaf(pa[q >> 1].y, gd.x, acc[d & 1][m].x);
-                            acc[d & 1][m].y = fmaf(pa[(q >> 1) + 1].x, gd.x, acc[d & 1][m].y);
+                            acc[m].x = fmaf(pa[q >> 1].y, gd.x, acc[m].x);
+                            acc[m].y = fmaf(pa[(q >> 1) + 1].x, gd.x, acc[m].y);
                         } else {
                             const float2 in = (q & 1) ? make_float2(pa[q >> 1].y, pa[(q >> 1) + 1].x) : pa[q >> 1];
-                            acc[d & 1][m] = fma2(in, gd, acc[d & 1][m]);
+                            acc[m] = fma2(in, gd, acc[m]);
                         }
                     }
                 }
 #pragma unroll
                 for (int m = 0; m < 4; ++m) {
-                    const float2 x = __fadd2_rn(acc[0][m], acc[1][m]);
+                    const float2 x = acc[m];
                     y[k][m] = fma2(x, gtr[2 * RT], st[0][k][m]);
 #pragma unroll
                     for (int j = 0; j < 2 * RT - 1; ++j) st[j][k][m] = fma2(x, gtr[2 * RT - 1 - j], st[j + 1][k][m]);

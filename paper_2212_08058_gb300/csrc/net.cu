@@ -405,7 +405,10 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
 // frames (3 x 32 channels; 3 x 16 for the last layer's one channel padded to 16).  Both operands
 // are read in the MN-major layout straight from the TMA copies of the channels-last activations:
 // [block][8-channel chunk][voxels][8 channels], where a core matrix is 8 voxels (K) x 8 channels
-// (16 bytes) and a shift by one voxel along w is a 16-byte offset of the descriptor's start.
+// (16 bytes) and a shift by one voxel along w is a 16-byte offset of the descriptor's start.  In
+// the descriptor of this no-swizzle MN-major layout the leading-dimension offset is the step
+// between groups of 8 voxels along K (128 bytes) and the stride-dimension offset the step between
+// 8-channel chunks along M or N (measured: the other assignment gives wrong sums).
 // Every unit of a CTA accumulates into the same TMEM columns; at the end the CTA writes its
 // partial sums to a scratch slice and a second kernel adds the slices in a fixed order.
 constexpr int WG_XV = MT + 2;                              // x voxels per row (w halo 1)
@@ -420,7 +423,9 @@ struct WgCfg {
     static constexpr int B_BYTES = 3 * NCO * WG_CHB;
     static constexpr int STAGE = WG_A_BYTES + B_BYTES;
     static constexpr int TMEM_COLS = 3 * N <= 256 ? 256 : 512;
-    static constexpr int SMEM = WG_NS * STAGE + (2 * WG_NS + 2) * 8 + 16 + 128;
+    // (the barriers sit after the stages; 8 KB more keep every descriptor offset inside the
+    // allocation whatever the operand reach)
+    static constexpr int SMEM = WG_NS * STAGE + (2 * WG_NS + 2) * 8 + 16 + 128 + 8192;
     static constexpr int PART = 3 * N * 128;               // floats of one CTA's partial sums
 };
 
@@ -520,8 +525,8 @@ wgrad_tc(const __grid_constant__ CUtensorMap xmap, const __grid_constant__ CUten
                 for (int dw = 0; dw < 3; ++dw)
 #pragma unroll
                     for (int kk = 0; kk < MT / 16; ++kk) {
-                        const uint64_t ad = sdesc(sa + (uint32_t)((kk * 16 + dw) * 16), WG_CHA, 128);
-                        const uint64_t bd = sdesc(sb + (uint32_t)(kk * 16 * 16), WG_CHB, 128);
+                        const uint64_t ad = sdesc(sa + (uint32_t)((kk * 16 + dw) * 16), 128, WG_CHA);
+                        const uint64_t bd = sdesc(sb + (uint32_t)(kk * 16 * 16), 128, WG_CHB);
                         umma(tmem + (uint32_t)(dw * C::N), ad, bd, ID, (i > 0 || kk > 0) ? 1u : 0u);
                     }
                 umma_commit(&empty[s]);
