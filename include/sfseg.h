@@ -363,6 +363,22 @@ int sfseg_iter_timing(sfseg_handle* h, double* ms, int64_t* launches);
  * Errors: INVALID_ARG (null count). */
 int sfseg_kernel_launches(int64_t* count);
 
+/* Eq. 8 for a volume split into parts (for example slabs along t, one per GPU): the squared
+ * norm of the next iterate is the sum of the parts' sums, so each part accumulates its own and
+ * the caller adds them across parts (an all-reduce) before every part divides by the root.
+ * sfseg_sumsq:     acc_dev[0] += sum_i x_i^2 over the n float32 values at x (device), summed in
+ *                  FP64 on the device (acc_dev: device double the caller zeroes first).
+ * sfseg_normalize: x_i *= 1 / sqrt(acc_dev[0]) for the n values at x (device).  A zero or
+ *                  non-finite acc_dev[0] leaves x multiplied by 0 and raises the handle's
+ *                  ZERO_NORM / NONFINITE flag (reported by sfseg_check).
+ * Both asynchronous on `stream`; h supplies the error flags only.  Errors: INVALID_ARG. */
+int sfseg_sumsq(sfseg_handle* h, const float* x, int64_t n, double* acc_dev, void* stream);
+int sfseg_normalize(sfseg_handle* h, float* x, int64_t n, const double* acc_dev, void* stream);
+
+/* Synchronises `stream` and reports (then clears) the handle's device-side error flags:
+ * TIMEOUT, NONFINITE (bad features or a non-finite norm), ZERO_NORM; OK if none is set. */
+int sfseg_check(sfseg_handle* h, void* stream);
+
 /* Which kernel ran the power-iteration steps (instrumentation; no counterpart in the paper).
  * The radii (1,3,3), (2,7,7), (1,4,4) and (1,2,2) run on the TMA-staged stencil kernel; other
  * radii, or a volume whose tensor maps the driver does not encode, run on the generic streaming

@@ -573,6 +573,31 @@ int sfseg_kernel_launches(int64_t* count) {
     return SFSEG_OK;
 }
 
+int sfseg_sumsq(sfseg_handle* h, const float* x, int64_t n, double* acc_dev, void* stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (!x || !acc_dev) return fail(SFSEG_ERR_INVALID_ARG, "null argument");
+    if (n < 0) return fail(SFSEG_ERR_INVALID_ARG, "n must be >= 0");
+    if (n == 0) return SFSEG_OK;
+    launch_sumsq(x, n, acc_dev, (cudaStream_t)stream);
+    SFSEG_LAUNCHED();
+    return SFSEG_OK;
+}
+
+int sfseg_normalize(sfseg_handle* h, float* x, int64_t n, const double* acc_dev, void* stream) {
+    if (int rc = check_handle(h)) return rc;
+    if (!x || !acc_dev) return fail(SFSEG_ERR_INVALID_ARG, "null argument");
+    if (n < 0) return fail(SFSEG_ERR_INVALID_ARG, "n must be >= 0");
+    if (n == 0) return SFSEG_OK;
+    launch_scale_inv_norm(x, n, acc_dev, h->flags, (cudaStream_t)stream);
+    SFSEG_LAUNCHED();
+    return SFSEG_OK;
+}
+
+int sfseg_check(sfseg_handle* h, void* stream) {
+    if (int rc = check_handle(h)) return rc;
+    return read_flags(h, (cudaStream_t)stream);
+}
+
 int sfseg_iterate_kernel_stats(int64_t* tma_steps, int64_t* generic_steps, char* last_kernel, int len) {
     if (!tma_steps || !generic_steps) return fail(SFSEG_ERR_INVALID_ARG, "null argument");
     if (last_kernel && len < 1) return fail(SFSEG_ERR_INVALID_ARG, "len must be >= 1");

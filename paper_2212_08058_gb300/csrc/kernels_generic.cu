@@ -341,6 +341,21 @@ __global__ void resid_kernel(const float* x, const float* y, int64_t n, double* 
     if (threadIdx.x == 0) atomicAdd(acc + 2, sa);
 }
 
+__global__ void sumsq_kernel(const float* x, int64_t n, double* acc) {
+    float a = 0.f;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a = fmaf(x[i], x[i], a);
+    const double sa = block_sum((double)a);
+    if (threadIdx.x == 0) atomicAdd(acc, sa);
+}
+
+void launch_sumsq(const float* x, int64_t n, double* acc, cudaStream_t s) {
+    int blocks = (int)((n + 255) / 256);
+    if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
+    if (blocks < 1) blocks = 1;
+    sumsq_kernel<<<blocks, 256, 0, s>>>(x, n, acc); count_launches(1);
+}
+
 void launch_dot2(const float* x, const float* y, int64_t n, double* acc, cudaStream_t s) {
     int blocks = (int)((n + 255) / 256);
     if (blocks > 8 * num_sms()) blocks = 8 * num_sms();

@@ -135,6 +135,8 @@ void launch_wait_probe(long long spins, int* flags, cudaStream_t s);
 // x *= 1/sqrt(*acc) over a caller-layout volume.
 void launch_scale_inv_norm(float* x, int64_t n, const double* acc, int* flags, cudaStream_t s);
 
+// acc[0] += sum x*x over n elements (FP64 block sums)
+void launch_sumsq(const float* x, int64_t n, double* acc, cudaStream_t s);
 // acc[0] += sum x*y, acc[1] += sum x*x  (x, y caller layout, n elements)
 void launch_dot2(const float* x, const float* y, int64_t n, double* acc, cudaStream_t s);
 // acc[2] += sum (y - rho x)^2 with rho = acc[0] / acc[1]

@@ -73,6 +73,9 @@ SIGNATURES = {
     "sfseg_enable_iter_timing": [_vp, _i],
     "sfseg_iter_timing": [_vp, _dp, ctypes.POINTER(ctypes.c_int64)],
     "sfseg_kernel_launches": [ctypes.POINTER(ctypes.c_int64)],
+    "sfseg_sumsq": [_vp, _vp, ctypes.c_int64, _vp, _vp],
+    "sfseg_normalize": [_vp, _vp, ctypes.c_int64, _vp, _vp],
+    "sfseg_check": [_vp, _vp],
     "sfseg_iterate_kernel_stats": [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
                                    ctypes.c_char_p, _i],
     "sfseg_net_create": [_i, ctypes.c_uint64, ctypes.POINTER(_vp)],
@@ -241,10 +244,11 @@ class PowerIteration:
             norms.ctypes.data_as(_dp) if norms is not None else None, _stream()))
         return (x, norms[:iters]) if return_norms else x
 
-    def apply(self, x: torch.Tensor, radius=(2, 7, 7), sigma=None) -> torch.Tensor:
-        """y = A x (the Eq. 7 operator, FP32)."""
+    def apply(self, x: torch.Tensor, radius=(2, 7, 7), sigma=None, out: torch.Tensor | None = None) -> torch.Tensor:
+        """y = A x (the Eq. 7 operator, FP32), into `out` when given."""
         self._check_volume(x, "x")
-        y = torch.empty_like(x)
+        y = torch.empty_like(x) if out is None else out
+        self._check_volume(y, "out")
         _check(lib().sfseg_apply(self._h, ctypes.byref(neighborhood(radius, sigma)), _ptr(x), _ptr(y), _stream()))
         return y
 
@@ -343,6 +347,20 @@ class PowerIteration:
         _check(lib().sfseg_warmstart(self._h, net._n, _ptr(features), _dtype_code(features), _ptr(x_coarse),
                                      _ptr(x0), _stream()))
         return x0
+
+    def sumsq(self, x: torch.Tensor, acc: torch.Tensor):
+        """acc[0] += sum(x^2) (FP64 on the device; x float32 contiguous, acc float64 on the device)."""
+        assert x.dtype == torch.float32 and x.is_contiguous() and acc.dtype == torch.float64
+        _check(lib().sfseg_sumsq(self._h, _ptr(x), x.numel(), _ptr(acc), _stream()))
+
+    def normalize(self, x: torch.Tensor, acc: torch.Tensor):
+        """x *= 1/sqrt(acc[0]) in place (Eq. 8)."""
+        assert x.dtype == torch.float32 and x.is_contiguous() and acc.dtype == torch.float64
+        _check(lib().sfseg_normalize(self._h, _ptr(x), x.numel(), _ptr(acc), _stream()))
+
+    def check(self):
+        """Synchronise and raise for device-side errors (TIMEOUT, NONFINITE, ZERO_NORM)."""
+        _check(lib().sfseg_check(self._h, _stream()))
 
     def selftest_wait(self, spins: int = 1000):
         """Run the bounded-wait failure path on purpose (sfseg_selftest_wait); raises SFSegError
