@@ -3,7 +3,7 @@
 // from a uniform vector or from S_m, Alg. 1 line 3; the network is an addition to the method.)
 //
 //   L1: C_in (<= 16, zero-padded to 16) -> 32, ReLU      L2, L3: 32 -> 32, ReLU
-//   L4: 32 -> 1 (computed as 16 output channels, only the first non-zero), softplus
+//   L4: 32 -> 1, softplus (its own kernel, conv_last_tc: the nine (dh, dw) taps on N)
 //
 // Activations are bf16 in channels-last layout [T][H][W][C]; every convolution is an implicit
 // GEMM on the 5th-generation tensor cores (tcgen05.mma, kind::f16, bf16 x bf16 -> fp32 in TMEM):
@@ -15,9 +15,10 @@
 // no-swizzle K-major layout ([8-channel chunk][3 frames][130 voxels][8 channels]); a tap's shift
 // along w is a 16-byte offset of the descriptor's start address, along t a 2080-byte offset.
 // All weights of the layer stay in shared memory.  One warp issues the TMA copies, one the MMAs,
-// four read each finished row's accumulator from TMEM, zero it, and run the epilogue.  The backward pass reuses the same kernel for the data gradient (flipped taps,
-// transposed channels, ReLU mask in the epilogue); the weight gradient is a reduction over
-// voxels on the CUDA cores.
+// four read each finished row's accumulator from TMEM, zero it, and run the epilogue.  The
+// backward pass reuses the same kernel for the data gradient (flipped taps, transposed
+// channels, ReLU mask in the epilogue); the weight gradient is its own tcgen05 kernel with the
+// voxels as the reduction dimension (wgrad_tc).
 #include <cuda.h>
 
 #include <cmath>
@@ -46,7 +47,7 @@ constexpr int NTHR = 192;               // 6 warps
 constexpr int kHrChoices[3] = {64, 32, 16};
 constexpr long long kSpin = 1ll << 26;
 
-enum Epi { EPI_RELU = 0, EPI_LAST = 1, EPI_MASK = 2 };
+enum Epi { EPI_RELU = 0, EPI_MASK = 2 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -168,8 +169,8 @@ struct ConvArgs {
     int HR;                       // output rows per CTA
     const __nv_bfloat16* wpack;   // packed weights (layout of the smem B operand)
     const float* bias;            // [COUT] or null
-    void* out;                    // EPI_RELU/EPI_MASK: bf16 [T][H][W][COUT]; EPI_LAST: float z [T][H][W]
-    float* out2;                  // EPI_LAST: x0 = softplus(z) [T][H][W]
+    void* out;                    // bf16 [T][H][W][COUT]
+    float* out2;                  // unused
     const __nv_bfloat16* mask;    // EPI_MASK: activation [T][H][W][COUT] whose sign gates the output
     int* flags;
 };
@@ -318,7 +319,7 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
         const int w = w0 + v;
         // the bias in registers, read once (the output stores may alias it as far as the compiler
         // knows, which would otherwise reload it for every row)
-        float bz[EPI == EPI_LAST ? 1 : (EPI == EPI_RELU ? COUT : 1)];
+        float bz[EPI == EPI_RELU ? COUT : 1];
 #pragma unroll
         for (int c = 0; c < (int)(sizeof(bz) / sizeof(float)); ++c) bz[c] = EPI == EPI_MASK ? 0.f : a.bias[c];
         for (int j = 0; j < nout; ++j) {
@@ -338,11 +339,7 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
             const int h = hs + j;
             if (w >= a.W) continue;
             const int64_t vox = ((int64_t)t * a.H + h) * a.W + w;
-            if constexpr (EPI == EPI_LAST) {
-                const float z = __uint_as_float(r[0]) + bz[0];
-                reinterpret_cast<float*>(a.out)[vox] = z;
-                a.out2[vox] = z > 20.f ? z : log1pf(expf(z));   // softplus
-            } else {
+            {
                 __nv_bfloat162 o[COUT / 2];
                 if constexpr (EPI == EPI_RELU) {
 #pragma unroll
@@ -392,6 +389,203 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
     tc_fence_after();
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
+}
+
+// -------------------------------------------------------------- last layer (32 -> 1, tcgen05)
+// The last layer has one output channel.  Stacking its three h-taps along N as the other layers
+// do would compute 16 padded outputs per tap; here the nine (dh, dw) taps of a frame offset
+// are the N dimension instead: for input row i (one h) and voxel v along w,
+//   D_i[v, 3 dh + dw] = sum_{dt, ci} x[t + dt - 1, i, v, ci] W[dt, dh, dw, ci]     (N = 9 -> 16)
+// six MMAs per input row (3 frames x 2 channel halves, M = 128 voxels, K = 16 channels), into
+// a ring of 16-column TMEM blocks, one per input row.  Output row j (input rows j, j+1, j+2 =
+// h - 1, h, h + 1) then takes z[w] = b + sum_{dh, dw} D_{j+dh}[w + dw - 1, 3 dh + dw]: the epilogue
+// sums the three rows in each lane, exchanges the three dw sums through shared memory (a lane's
+// neighbours along w may sit in another warp) and adds them.  M = 128 voxels cover 126 outputs
+// and their w halo, so the tiles are 126 voxels wide.
+constexpr int LT_W = MT - 2;                 // outputs per tile along w
+constexpr int LT_R = 16;                     // TMEM blocks (input rows) in the ring
+constexpr int LT_COLS = LT_R * 16;           // 256: two CTAs can share an SM's tensor memory
+constexpr int LT_SLOT = 4 * CHUNK_BYTES;     // one input row: 4 chunks of 8 channels x 3 frames
+constexpr int LT_BBYTES = 3 * 2 * 2 * 16 * 16;   // [dt][ks][chunk][16 taps][8 channels] bf16
+
+struct LastArgs {
+    int T, H, W, HR;
+    const __nv_bfloat16* wtap;   // packed taps, LT_BBYTES bytes
+    const float* bias;           // [1]
+    float* z;                    // [T][H][W]
+    float* x0;                   // softplus(z), [T][H][W]
+    int* flags;
+};
+
+struct LastCfg {
+    static constexpr int NB = 2 * NSLOT + 2 * LT_R + 2;
+    static constexpr int XS = 2 * 3 * 128 * 4 + 2 * 4 * 4;   // the dw sums of two rows, and each epilogue
+                                                           // warp's wait status (double buffer)
+    static constexpr int SMEM = LT_BBYTES + NSLOT * LT_SLOT + XS + NB * 8 + 16 + 128;
+};
+
+__global__ void __launch_bounds__(NTHR, 1)
+conv_last_tc(const __grid_constant__ CUtensorMap xin, LastArgs a) {
+    extern __shared__ __align__(128) unsigned char sm_raw[];
+    unsigned char* sm = (unsigned char*)(((uintptr_t)sm_raw + 127) & ~(uintptr_t)127);
+    unsigned char* wsm = sm;
+    unsigned char* ring = sm + LT_BBYTES;
+    float* xs = reinterpret_cast<float*>(ring + NSLOT * LT_SLOT);   // [2][3][128]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(ring + NSLOT * LT_SLOT + LastCfg::XS);
+    uint64_t* full = bar;
+    uint64_t* empty = bar + NSLOT;
+    uint64_t* accf = bar + 2 * NSLOT;            // [LT_R]: input row's D complete
+    uint64_t* acce = bar + 2 * NSLOT + LT_R;     // [LT_R]: block read by every output row that needs it
+    uint64_t* wbar = bar + 2 * NSLOT + 2 * LT_R;
+    uint64_t* drain = wbar + 1;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + LastCfg::NB);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int HR = a.HR;
+    const int nws = (a.W + LT_W - 1) / LT_W, nhr = (a.H + HR - 1) / HR;
+    int item = blockIdx.x;
+    const int hr = item % nhr;
+    item /= nhr;
+    const int ws = item % nws;
+    const int t = item / nws;
+    const int w0 = ws * LT_W, hs = hr * HR, he = min(a.H, hs + HR);
+    const int nout = he - hs, nin = nout + 2;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < NSLOT; ++i) {
+            mb_init(&full[i], 1);
+            mb_init(&empty[i], 1);
+        }
+        for (int i = 0; i < LT_R; ++i) {
+            mb_init(&accf[i], 1);
+            mb_init(&acce[i], 4);
+        }
+        mb_init(wbar, 1);
+        mb_init(drain, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(LT_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    int issued = 0;
+    if (warp == 0) {
+        if (lane == 0) {   // ---------------- producer: the taps, then the input rows
+            mb_expect(wbar, LT_BBYTES);
+            bulk_g2s(wsm, a.wtap, LT_BBYTES, wbar);
+            for (int i = 0; i < nin; ++i) {
+                const int s = i % NSLOT;
+                if (i >= NSLOT && !mb_wait(&empty[s], (uint32_t)((i / NSLOT - 1) & 1), a.flags)) break;
+                issued = i + 1;
+                mb_expect(&full[s], 4 * CHUNK_DATA);
+                unsigned char* dst = ring + s * LT_SLOT;
+                for (int k = 0; k < 4; ++k) tma4(dst + k * CHUNK_BYTES, &xin, &full[s], 8 * k, w0 - 1, hs - 1 + i, t - 1);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {   // ---------------- MMA issuer: six MMAs per input row into its block
+            bool ok = mb_wait(wbar, 0, a.flags);
+            const uint32_t wbase = su32(wsm), rbase = su32(ring);
+            constexpr uint32_t ID = idesc_bf16(16);
+            for (int i = 0; ok && i < nin; ++i) {
+                ok = mb_wait(&full[i % NSLOT], (uint32_t)((i / NSLOT) & 1), a.flags);
+                if (ok && i >= LT_R) ok = mb_wait(&acce[i % LT_R], (uint32_t)(((i - LT_R) / LT_R) & 1), a.flags);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)((i % LT_R) * 16);
+                const uint64_t a0 = sdesc(rbase + (uint32_t)((i % NSLOT) * LT_SLOT), CHUNK_BYTES, 128);
+#pragma unroll
+                for (int dt = 0; dt < 3; ++dt)
+#pragma unroll
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint64_t ad = a0 + (uint64_t)((2 * ks * CHUNK_BYTES + dt * RW * 16) >> 4);
+                        const uint64_t bd = sdesc(wbase + (uint32_t)((dt * 2 + ks) * 512), 256, 128);
+                        umma(d, ad, bd, ID, (dt | ks) ? 1u : 0u);
+                    }
+                umma_commit(&empty[i % NSLOT]);
+                umma_commit(&accf[i % LT_R]);
+            }
+        }
+    } else {   // ---------------- epilogue: warps 2..5
+        const int q = warp & 3;
+        const int l = q * 32 + lane;            // TMEM lane = voxel w0 - 1 + l
+        const float b = a.bias[0];
+        for (int j = 0; j < nout; ++j) {
+            float sdw[3] = {0.f, 0.f, 0.f};
+            bool ok = true;
+#pragma unroll
+            for (int dh = 0; dh < 3; ++dh) {
+                const int r = j + dh;           // input row of offset dh
+                ok = ok && mb_wait(&accf[r % LT_R], (uint32_t)((r / LT_R) & 1), a.flags);
+                tc_fence_after();
+                uint32_t v[16];
+                tmem_ld<16>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((r % LT_R) * 16), v);
+                tmem_ld_wait();
+#pragma unroll
+                for (int dw = 0; dw < 3; ++dw) sdw[dw] += __uint_as_float(v[3 * dh + dw]);
+            }
+            // input row j is needed by no later output row
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mb_arrive(&acce[j % LT_R]);
+            float* xb = xs + (j & 1) * 3 * 128;
+            int* okb = reinterpret_cast<int*>(xs + 2 * 3 * 128) + (j & 1) * 4;
+#pragma unroll
+            for (int dw = 0; dw < 3; ++dw) xb[dw * 128 + l] = sdw[dw];
+            if (lane == 0) okb[q] = ok ? 1 : 0;
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            // the four warps leave together if any of their waits gave up
+            if (!(okb[0] & okb[1] & okb[2] & okb[3])) break;
+            const int h = hs + j, w = w0 + l;
+            if (l < LT_W && w < a.W) {
+                const float z = b + xb[l] + xb[128 + l + 1] + xb[256 + l + 2];
+                const int64_t vox = ((int64_t)t * a.H + h) * a.W + w;
+                a.z[vox] = z;
+                a.x0[vox] = z > 20.f ? z : log1pf(expf(z));   // softplus
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (*reinterpret_cast<volatile int*>(a.flags) & kFlagTimeout) {
+        if (warp == 0 && lane == 0) {
+            mb_settle(wbar, 0);
+            for (int s = 0; s < NSLOT && s < issued; ++s) {
+                const int last = s + ((issued - 1 - s) / NSLOT) * NSLOT;
+                mb_settle(&full[s], (uint32_t)((last / NSLOT) & 1));
+            }
+        } else if (warp == 1 && lane == 0) {
+            umma_commit(drain);
+            mb_settle(drain, 0);
+        }
+        __syncthreads();
+    }
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(LT_COLS) : "memory");
+}
+
+// Taps of the last layer for conv_last_tc: out[((dt * 2 + ks) * 2 + chunk) * 16 + n][e] =
+// W[0][9 dt + 3 dh + dw][16 ks + 8 chunk + e] for n = 3 dh + dw < 9, zero for n >= 9.
+__global__ void pack_last_taps(const float* W, __nv_bfloat16* out) {
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < LT_BBYTES / 2; idx += gridDim.x * blockDim.x) {
+        int r = idx;
+        const int e = r % 8; r /= 8;
+        const int n = r % 16; r /= 16;
+        const int ch = r % 2; r /= 2;
+        const int ks = r % 2; r /= 2;
+        const int dt = r;
+        float v = 0.f;
+        if (n < 9) v = W[(9 * dt + n) * 32 + ks * 16 + ch * 8 + e];
+        out[idx] = __float2bfloat16_rn(v);
+    }
 }
 
 // ------------------------------------------------------------------ weight gradient (tcgen05)
@@ -849,13 +1043,42 @@ int run_conv(const void* in, int T, int H, int W, const __nv_bfloat16* wpack, co
     return SFSEG_OK;
 }
 
+// The last layer (32 -> 1) on its own kernel, 126-voxel tiles along w (conv_last_tc).
+int run_last(const __nv_bfloat16* in, int T, int H, int W, const __nv_bfloat16* wtap, const float* bias, float* z,
+             float* x0, int* flags, cudaStream_t s) {
+    CUtensorMap m;
+    if (!act_map(&m, in, 32, T, H, W)) return nfail(SFSEG_ERR_CUDA, "tensor map encoding failed");
+    static bool attr = false;
+    if (!attr) {
+        NET_CUDA(cudaFuncSetAttribute(conv_last_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, LastCfg::SMEM));
+        attr = true;
+    }
+    LastArgs a;
+    a.T = T; a.H = H; a.W = W;
+    a.wtap = wtap; a.bias = bias; a.z = z; a.x0 = x0; a.flags = flags;
+    int items = 0;
+    for (int hr : kHrChoices) {
+        a.HR = hr;
+        items = T * ((W + LT_W - 1) / LT_W) * ((H + hr - 1) / hr);
+        if (items >= 8 * num_sms()) break;   // two CTAs per SM, four waves
+    }
+    conv_last_tc<<<items, NTHR, LastCfg::SMEM, s>>>(m, a);
+    count_launches(1);
+    NET_CUDA(cudaGetLastError());
+    return SFSEG_OK;
+}
+
 int pack_all(sfseg_net* n, cudaStream_t s) {
     if (n->packed) return SFSEG_OK;
     const int cinp[4] = {16, 32, 32, 32}, coutp[4] = {32, 32, 32, 16};
     for (int l = 0; l < 4; ++l) {
-        const int total = 27 * (cinp[l] / 16) * 2 * coutp[l] * 8;
-        pack_weights<<<(total + 255) / 256, 256, 0, s>>>(n->p + n->off[2 * l], kCout[l], layer_cin(n, l), coutp[l],
-                                                         cinp[l], 0, n->wf[l]);
+        if (l == 3) {   // the last layer's forward taps in conv_last_tc's layout
+            pack_last_taps<<<(LT_BBYTES / 2 + 255) / 256, 256, 0, s>>>(n->p + n->off[6], n->wf[3]);
+        } else {
+            const int total = 27 * (cinp[l] / 16) * 2 * coutp[l] * 8;
+            pack_weights<<<(total + 255) / 256, 256, 0, s>>>(n->p + n->off[2 * l], kCout[l], layer_cin(n, l),
+                                                             coutp[l], cinp[l], 0, n->wf[l]);
+        }
         count_launches(1);
         if (l > 0) {   // data gradient of layer l: input = dz of its output (COUT_l channels, padded)
             const int ci2 = l == 3 ? 16 : 32;
@@ -901,8 +1124,7 @@ int net_forward(sfseg_net* n, const void* feats, int dtype, int C, const float* 
     if (int rc = run_conv<32, 32, EPI_RELU>(n->a2, T, H, W, n->wf[2], n->p + n->off[5], a3, nullptr, nullptr,
                                             n->flags, s))
         return rc;
-    if (int rc = run_conv<32, 16, EPI_LAST>(a3, T, H, W, n->wf[3], n->p + n->off[7], n->z4, n->x0, nullptr,
-                                            n->flags, s))
+    if (int rc = run_last(a3, T, H, W, n->wf[3], n->p + n->off[7], n->z4, n->x0, n->flags, s))
         return rc;
     n->have_fwd = true;
     return SFSEG_OK;
@@ -1117,7 +1339,7 @@ int sfseg_net_layer_forward(sfseg_net* n, int layer, const void* in, int T, int 
     const __nv_bfloat16* x = (const __nv_bfloat16*)in;
     if (layer == 0) return run_conv<16, 32, EPI_RELU>(x, T, H, W, n->wf[0], b, out, nullptr, nullptr, n->flags, s);
     if (layer < 3) return run_conv<32, 32, EPI_RELU>(x, T, H, W, n->wf[layer], b, out, nullptr, nullptr, n->flags, s);
-    return run_conv<32, 16, EPI_LAST>(x, T, H, W, n->wf[3], b, out, out2, nullptr, n->flags, s);
+    return run_last(x, T, H, W, n->wf[3], b, (float*)out, out2, n->flags, s);
 }
 
 int sfseg_net_layer_backward(sfseg_net* n, int layer, const void* in, const void* dz, int T, int H, int W,

@@ -50,11 +50,12 @@ def _points(T, H, W, HR, seed, n_random=40):
         hs.update({base - 1, base, base + 1})
     for j in (15, 16, 17, 31, 32, 33):                   # ring wraps inside the second tile
         hs.add(HR + j)
-    ws = {0, 1, 126, 127, 128, 129, 255, 256, W - 129, W - 128, W - 2, W - 1}
+    # 128-voxel tiles of the hidden layers, 126-voxel tiles of the last layer
+    ws = {0, 1, 125, 126, 127, 128, 129, 251, 252, 255, 256, W - 129, W - 128, W - 2, W - 1}
     pts = set()
     for h in hs:
         for t in (0, T // 2, T - 1):
-            for w in (0, 127, 128, W - 1):
+            for w in (0, 125, 126, 127, 128, W - 1):
                 pts.add((t, h, w))
     for w in ws:
         for t in (0, T - 1):
