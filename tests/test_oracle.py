@@ -368,6 +368,29 @@ def test_conv3d_backward_matches_finite_differences():
     np.testing.assert_allclose(db, c.sum(axis=(0, 1, 2)), rtol=1e-12)
 
 
+def test_cosine_loss_closed_forms():
+    """The warm-start training loss 1 - cos(x0, target): 0 for any positive multiple of the
+    target, 1 for orthogonal vectors, 1 - 1/sqrt(2) at 45 degrees, invariant to scaling either
+    argument; its gradient is orthogonal to x0 (the loss does not change along x0) and equals
+    central differences."""
+    t = np.array([0.0, 3.0, 4.0])
+    assert oracle.cosine_loss(2.5 * t, t)[0] == pytest.approx(0.0, abs=1e-15)
+    assert oracle.cosine_loss(np.array([1.0, 0.0, 0.0]), t)[0] == pytest.approx(1.0)
+    a, b = np.array([1.0, 0.0]), np.array([1.0, 1.0])
+    assert oracle.cosine_loss(a, b)[0] == pytest.approx(1.0 - 1.0 / np.sqrt(2.0))
+    rng = np.random.default_rng(12)
+    x, g = rng.uniform(0.1, 1.0, 7), rng.uniform(0.1, 1.0, 7)
+    l0, dx = oracle.cosine_loss(x, g)
+    assert oracle.cosine_loss(4.0 * x, 0.5 * g)[0] == pytest.approx(l0, rel=1e-13)
+    assert abs(np.dot(dx, x)) < 1e-13
+    h = 1e-7
+    for i in range(7):
+        e = np.zeros(7)
+        e[i] = h
+        fd = (oracle.cosine_loss(x + e, g)[0] - oracle.cosine_loss(x - e, g)[0]) / (2 * h)
+        assert abs(fd - dx[i]) < 1e-7
+
+
 def test_warmstart_network_gradient_matches_finite_differences():
     rng = np.random.default_rng(10)
     C, T, H, W = 3, 3, 4, 5
