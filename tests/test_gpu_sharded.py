@@ -42,3 +42,33 @@ def test_lockstep_slabs_match_whole_video(sf, parts, radius):
     with sf.PowerIteration(3, T, H, W) as h:
         xw = h.power_iterate(feats, w, 0.0, radius, iters=iters).cpu().numpy()
     assert np.abs(x - xw).max() <= TOL_F32
+
+
+def test_distributed_driver_single_rank_nccl(sf):
+    """The distributed driver through NCCL with one rank (its all-reduce on the device; the
+    halo exchange needs neighbours, which need more GPUs than this run has), against
+    sfseg_power_iterate on the same volume."""
+    import os
+    import socket
+
+    import torch.distributed as dist
+    T, H, W, iters, radius = 16, 64, 100, 10, (2, 7, 7)
+    V, _, w = synth.multichannel(T, H, W, C=2, seed=3101)
+    feats = torch.from_numpy(V).cuda()
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("nccl", rank=0, world_size=1, device_id=torch.device("cuda", 0))
+    try:
+        slab = sharded.Slab(T, 1, 0, radius[0])
+        be = sharded.LibraryBackend(feats, w, 0.0, radius)
+        x, norms = sharded.power_iterate_distributed(be, slab, torch.ones((T, H, W), device="cuda"), iters)
+        torch.cuda.synchronize()
+        be.close()
+    finally:
+        dist.destroy_process_group()
+    with sf.PowerIteration(2, T, H, W) as h:
+        xw, nuw = h.power_iterate(feats, w, 0.0, radius, iters=iters, return_norms=True)
+    assert float((x - xw).abs().max()) <= TOL_F32
+    np.testing.assert_allclose(norms.cpu().numpy(), nuw, rtol=1e-5)
