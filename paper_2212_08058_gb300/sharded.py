@@ -146,7 +146,7 @@ def power_iterate_distributed(backend, slab: Slab, x_own, iters: int, group=None
         backend.normalize(_own(y, slab), acc)
         x, y = y, x
     backend.check()
-    return _own(x, slab).clone(), norms[:iters].sqrt()
+    return _own(x, slab).clone(), norms[:iters].cpu().numpy() ** 0.5
 
 
 def _exchange(x, slab: Slab, group=None):
@@ -171,13 +171,13 @@ def _exchange(x, slab: Slab, group=None):
 def power_iterate_lockstep(backends, slabs, xs_own, iters: int):
     """The same steps for several parts in one process (in turn, on one device): the halo
     frames are copied between the parts' extended slabs and the norm is the sum of their
-    partial sums.  Returns ([x_own of each part], device tensor of the norms)."""
+    partial sums (each part's sum of squares accumulates into one device scalar).  Returns
+    ([x_own of each part], numpy array of the norms)."""
     import torch
 
     n = len(slabs)
     xs = [b.empty() for b in backends]
     ys = [b.empty() for b in backends]
-    accs = [b.acc() for b in backends]
     total = backends[0].acc()
     norms = torch.zeros(max(iters, 1), dtype=torch.float64, device=total.device)
     for i in range(n):
@@ -187,9 +187,7 @@ def power_iterate_lockstep(backends, slabs, xs_own, iters: int):
     def reduce_and_normalize(vs, k):
         total.zero_()
         for i in range(n):
-            accs[i].zero_()
-            backends[i].sumsq(_own(vs[i], slabs[i]), accs[i])
-            total.add_(accs[i])
+            backends[i].sumsq(_own(vs[i], slabs[i]), total)
         if k >= 0:
             norms[k] = total[0]
         for i in range(n):
@@ -209,7 +207,7 @@ def power_iterate_lockstep(backends, slabs, xs_own, iters: int):
         xs, ys = ys, xs
     for b in backends:
         b.check()
-    return [_own(xs[i], slabs[i]).clone() for i in range(n)], norms[:iters].sqrt()
+    return [_own(xs[i], slabs[i]).clone() for i in range(n)], norms[:iters].cpu().numpy() ** 0.5
 
 
 def halo_bytes_per_iteration(slab: Slab, H: int, W: int) -> int:

@@ -121,12 +121,24 @@ def _input16(T, H, W, seed):
     return x
 
 
-@pytest.mark.parametrize("shape,hr", [((8, 1024, 640), 64), ((32, 256, 512), 32)], ids=["rows64", "rows32"])
+def _last_layer_rows(T, H, W):
+    """The row count per CTA of the last layer's kernel (126-voxel tiles, two CTAs per SM)."""
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    for hr in (64, 32, 16):
+        if T * -(-W // 126) * -(-H // hr) >= 8 * nsm:
+            return hr
+    return 16
+
+
+@pytest.mark.parametrize("shape,hr", [((8, 1024, 640), 64), ((32, 256, 512), 32), ((32, 512, 512), 64)],
+                         ids=["rows64", "rows32", "rows64_last_layer_too"])
 def test_layers_at_production_tile_heights(sf, shape, hr):
     """Each layer's output at sampled voxels against the oracle's convolution of the GPU layer's
-    own input, at the tile height the launch picks for this volume."""
+    own input, at the tile height the launch picks for this volume (the last layer's kernel
+    picks its own: 32 rows for the first two volumes, 64 for the third, as at 1080p)."""
     T, H, W = shape
     assert _tile_rows(T, H, W) == hr
+    assert _last_layer_rows(T, H, W) == (64 if shape == (32, 512, 512) else 32)
     net = sf.WarmStartNet(C_IN, seed=11)
     params = _layer_params(net)
     x16 = _input16(T, H, W, 900 + hr)

@@ -32,7 +32,7 @@ def test_lockstep_slabs_match_whole_video(sf, parts, radius):
     xs0 = [torch.ones((s.t1 - s.t0, H, W), device="cuda") for s in slabs]
     xs, norms = sharded.power_iterate_lockstep(backends, slabs, xs0, iters)
     x = torch.cat(xs).cpu().numpy().astype(np.float64)
-    nu = norms.cpu().numpy()
+    nu = norms
     for b in backends:
         b.close()
     f = oracle.combine(V.astype(np.float64), w)
@@ -71,4 +71,4 @@ def test_distributed_driver_single_rank_nccl(sf):
     with sf.PowerIteration(2, T, H, W) as h:
         xw, nuw = h.power_iterate(feats, w, 0.0, radius, iters=iters, return_norms=True)
     assert float((x - xw).abs().max()) <= TOL_F32
-    np.testing.assert_allclose(norms.cpu().numpy(), nuw, rtol=1e-5)
+    np.testing.assert_allclose(norms, nuw, rtol=1e-5)

@@ -63,7 +63,7 @@ def _worker(rank, world, port, T, H, W, radius, iters, out):
     be = OracleBackend(f[slab.e0:slab.e1], radius)
     x_own = torch.ones((slab.t1 - slab.t0, H, W), dtype=torch.float64)
     x, norms = sharded.power_iterate_distributed(be, slab, x_own, iters)
-    out[rank] = (slab.t0, slab.t1, x.numpy(), norms.numpy())
+    out[rank] = (slab.t0, slab.t1, x.numpy(), norms)
     dist.barrier()
     dist.destroy_process_group()
 
