@@ -191,7 +191,10 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
     const int w0 = blockIdx.x * TW, h0 = blockIdx.y * TH;
     const int t0 = blockIdx.z * P.tchunk;
     const int t1 = min(t0 + P.tchunk, g.T);
-    const int tstart = t0 - RT, tend = t1 + RT;
+    // Frames before t = 0 are zero (zero padding): they would add exactly nothing to the
+    // t-filter state, so the first chunk starts at frame 0.  Frames after the last are still
+    // streamed, to flush the last rt output frames.
+    const int tstart = max(t0 - RT, 0), tend = t1 + RT;
 
     const float s = inv_norm_from(P.acc_in, P.flags);
     const float2 s2 = f2(s);

@@ -170,7 +170,6 @@ struct ConvArgs {
     const __nv_bfloat16* wpack;   // packed weights (layout of the smem B operand)
     const float* bias;            // [COUT] or null
     void* out;                    // bf16 [T][H][W][COUT]
-    float* out2;                  // unused
     const __nv_bfloat16* mask;    // EPI_MASK: activation [T][H][W][COUT] whose sign gates the output
     int* flags;
 };
@@ -1018,7 +1017,7 @@ int ensure_ws(sfseg_net* n, int64_t N, bool train) {
 
 template <int CIN, int COUT, int EPI>
 int run_conv(const void* in, int T, int H, int W, const __nv_bfloat16* wpack, const float* bias, void* out,
-             float* out2, const __nv_bfloat16* mask, int* flags, cudaStream_t s) {
+             const __nv_bfloat16* mask, int* flags, cudaStream_t s) {
     using Cf = ConvCfg<CIN, COUT>;
     CUtensorMap m;
     if (!act_map(&m, in, CIN, T, H, W)) return nfail(SFSEG_ERR_CUDA, "tensor map encoding failed");
@@ -1030,7 +1029,7 @@ int run_conv(const void* in, int T, int H, int W, const __nv_bfloat16* wpack, co
     }
     ConvArgs a;
     a.T = T; a.H = H; a.W = W;
-    a.wpack = wpack; a.bias = bias; a.out = out; a.out2 = out2; a.mask = mask; a.flags = flags;
+    a.wpack = wpack; a.bias = bias; a.out = out; a.mask = mask; a.flags = flags;
     int items = 0;
     for (int hr : kHrChoices) {
         a.HR = hr;
@@ -1115,13 +1114,13 @@ int net_forward(sfseg_net* n, const void* feats, int dtype, int C, const float* 
         to_channels_last<__nv_bfloat16><<<blocks_for(N), 256, 0, s>>>((const __nv_bfloat16*)feats, C, extra, N,
                                                                        n->x16);
     count_launches(1);
-    if (int rc = run_conv<16, 32, EPI_RELU>(n->x16, T, H, W, n->wf[0], n->p + n->off[1], n->a1, nullptr, nullptr,
+    if (int rc = run_conv<16, 32, EPI_RELU>(n->x16, T, H, W, n->wf[0], n->p + n->off[1], n->a1, nullptr,
                                             n->flags, s))
         return rc;
-    if (int rc = run_conv<32, 32, EPI_RELU>(n->a1, T, H, W, n->wf[1], n->p + n->off[3], n->a2, nullptr, nullptr,
+    if (int rc = run_conv<32, 32, EPI_RELU>(n->a1, T, H, W, n->wf[1], n->p + n->off[3], n->a2, nullptr,
                                             n->flags, s))
         return rc;
-    if (int rc = run_conv<32, 32, EPI_RELU>(n->a2, T, H, W, n->wf[2], n->p + n->off[5], a3, nullptr, nullptr,
+    if (int rc = run_conv<32, 32, EPI_RELU>(n->a2, T, H, W, n->wf[2], n->p + n->off[5], a3, nullptr,
                                             n->flags, s))
         return rc;
     if (int rc = run_last(a3, T, H, W, n->wf[3], n->p + n->off[7], n->z4, n->x0, n->flags, s))
@@ -1306,15 +1305,15 @@ int sfseg_net_backward(sfseg_net* n, const void* features, int dtype, int C, con
     count_launches(2);
     // layer 4
     if (int rc = wgrad(n, 3, n->dz16, 16, n->a3, 32, T, H, W, s)) return rc;
-    if (int rc = run_conv<16, 32, EPI_MASK>(n->dz16, T, H, W, n->wb[3], nullptr, n->dza, nullptr, n->a3, n->flags, s))
+    if (int rc = run_conv<16, 32, EPI_MASK>(n->dz16, T, H, W, n->wb[3], nullptr, n->dza, n->a3, n->flags, s))
         return rc;
     // layer 3
     if (int rc = wgrad(n, 2, n->dza, 32, n->a2, 32, T, H, W, s)) return rc;
-    if (int rc = run_conv<32, 32, EPI_MASK>(n->dza, T, H, W, n->wb[2], nullptr, n->dzb, nullptr, n->a2, n->flags, s))
+    if (int rc = run_conv<32, 32, EPI_MASK>(n->dza, T, H, W, n->wb[2], nullptr, n->dzb, n->a2, n->flags, s))
         return rc;
     // layer 2
     if (int rc = wgrad(n, 1, n->dzb, 32, n->a1, 32, T, H, W, s)) return rc;
-    if (int rc = run_conv<32, 32, EPI_MASK>(n->dzb, T, H, W, n->wb[1], nullptr, n->dza, nullptr, n->a1, n->flags, s))
+    if (int rc = run_conv<32, 32, EPI_MASK>(n->dzb, T, H, W, n->wb[1], nullptr, n->dza, n->a1, n->flags, s))
         return rc;
     // layer 1
     if (int rc = wgrad(n, 0, n->dza, 32, n->x16, 16, T, H, W, s)) return rc;
@@ -1337,8 +1336,8 @@ int sfseg_net_layer_forward(sfseg_net* n, int layer, const void* in, int T, int 
     if (int rc = pack_all(n, s)) return rc;
     const float* b = n->p + n->off[2 * layer + 1];
     const __nv_bfloat16* x = (const __nv_bfloat16*)in;
-    if (layer == 0) return run_conv<16, 32, EPI_RELU>(x, T, H, W, n->wf[0], b, out, nullptr, nullptr, n->flags, s);
-    if (layer < 3) return run_conv<32, 32, EPI_RELU>(x, T, H, W, n->wf[layer], b, out, nullptr, nullptr, n->flags, s);
+    if (layer == 0) return run_conv<16, 32, EPI_RELU>(x, T, H, W, n->wf[0], b, out, nullptr, n->flags, s);
+    if (layer < 3) return run_conv<32, 32, EPI_RELU>(x, T, H, W, n->wf[layer], b, out, nullptr, n->flags, s);
     return run_last(x, T, H, W, n->wf[3], b, (float*)out, out2, n->flags, s);
 }
 
@@ -1356,8 +1355,8 @@ int sfseg_net_layer_backward(sfseg_net* n, int layer, const void* in, const void
     if (int rc = wgrad_into(n, layer, cin, g, dzc, x, cinp, T, H, W, dW_out, db_out, s)) return rc;
     if (dx_out && layer > 0) {
         if (layer == 3)
-            return run_conv<16, 32, EPI_MASK>(g, T, H, W, n->wb[3], nullptr, dx_out, nullptr, x, n->flags, s);
-        return run_conv<32, 32, EPI_MASK>(g, T, H, W, n->wb[layer], nullptr, dx_out, nullptr, x, n->flags, s);
+            return run_conv<16, 32, EPI_MASK>(g, T, H, W, n->wb[3], nullptr, dx_out, x, n->flags, s);
+        return run_conv<32, 32, EPI_MASK>(g, T, H, W, n->wb[layer], nullptr, dx_out, x, n->flags, s);
     }
     return SFSEG_OK;
 }
