@@ -136,19 +136,50 @@ __global__ void adjoint_combine_state_kernel(const float* f, const float* vg, co
                                              const double* dsum, Geom g, float* gz, float* vg_next) {
     const float sk = inv_norm_from(acc_k, nullptr);
     const float dot = sk * (float)*dsum;
-    for_each_voxel(g, [&](int64_t, int64_t j) {
-        const float v = Vk[j];
-        gz[j] += (1.f - f[j]) * (vg[j] * qx[j] + sk * v * qg[j]);
-        if (vg_next) vg_next[j] = sk * (Gk[j] - sk * dot * v);
-    });
+    // rows (t, h) over the blocks, four columns per thread (internal rows start 128-byte
+    // aligned), the ragged end of a row one column at a time
+    const int64_t rows = (int64_t)g.T * g.H;
+    const int w4 = g.W / 4;
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int64_t j0 = row * g.pitch;
+        for (int c = threadIdx.x; c < w4; c += blockDim.x) {
+            const int64_t j = j0 + 4 * c;
+            const float4 v = *reinterpret_cast<const float4*>(Vk + j);
+            const float4 ff = *reinterpret_cast<const float4*>(f + j);
+            const float4 a = *reinterpret_cast<const float4*>(vg + j);
+            const float4 b = *reinterpret_cast<const float4*>(qx + j);
+            const float4 q = *reinterpret_cast<const float4*>(qg + j);
+            float4 z = *reinterpret_cast<const float4*>(gz + j);
+            z.x += (1.f - ff.x) * (a.x * b.x + sk * v.x * q.x);
+            z.y += (1.f - ff.y) * (a.y * b.y + sk * v.y * q.y);
+            z.z += (1.f - ff.z) * (a.z * b.z + sk * v.z * q.z);
+            z.w += (1.f - ff.w) * (a.w * b.w + sk * v.w * q.w);
+            *reinterpret_cast<float4*>(gz + j) = z;
+            if (vg_next) {
+                const float4 G = *reinterpret_cast<const float4*>(Gk + j);
+                *reinterpret_cast<float4*>(vg_next + j) =
+                    make_float4(sk * (G.x - sk * dot * v.x), sk * (G.y - sk * dot * v.y), sk * (G.z - sk * dot * v.z),
+                                sk * (G.w - sk * dot * v.w));
+            }
+        }
+        for (int w = 4 * w4 + threadIdx.x; w < g.W; w += blockDim.x) {
+            const int64_t j = j0 + w;
+            const float v = Vk[j];
+            gz[j] += (1.f - f[j]) * (vg[j] * qx[j] + sk * v * qg[j]);
+            if (vg_next) vg_next[j] = sk * (Gk[j] - sk * dot * v);
+        }
+    }
 }
 
 void launch_adjoint_combine_state(const float* f32, const float* vg, const float* qx, const float* Vk,
                                   const float* qg, const float* Gk, const double* acc_k, const double* dsum, Geom g,
                                   float* gz, float* vg_next, cudaStream_t s) {
-    const RowLaunch rl = row_launch(g, num_sms(), 8);
-    adjoint_combine_state_kernel<<<rl.blocks, rl.threads, 0, s>>>(f32, vg, qx, Vk, qg, Gk, acc_k, dsum, g, gz,
-                                                                   vg_next);
+    const int w4 = g.W / 4;
+    const int threads = w4 >= 128 ? 128 : (w4 > 0 ? (w4 + 31) / 32 * 32 : 32);
+    const int64_t rows = (int64_t)g.T * g.H;
+    const int64_t cap = (int64_t)16 * num_sms();
+    const int blocks = (int)(rows < cap ? (rows > 0 ? rows : 1) : cap);
+    adjoint_combine_state_kernel<<<blocks, threads, 0, s>>>(f32, vg, qx, Vk, qg, Gk, acc_k, dsum, g, gz, vg_next);
     count_launches(1);
 }
 
