@@ -306,45 +306,70 @@ void launch_to_bf16(const float* a, __nv_bfloat16* b, int64_t n, cudaStream_t s)
 }
 
 // ------------------------------------------------------------------------- reductions
-__global__ void scale_inv_norm_kernel(float* x, int64_t n, const double* acc, int* flags) {
+__global__ void scale_inv_norm_kernel(float* x, int64_t n, bool vec, const double* acc, int* flags) {
     const float s = inv_norm_from(acc, flags);
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        x[i] *= s;
+    for_each_flat(
+        n, vec,
+        [&](int64_t i) {
+            float4 v = reinterpret_cast<float4*>(x)[i];
+            v.x *= s, v.y *= s, v.z *= s, v.w *= s;
+            reinterpret_cast<float4*>(x)[i] = v;
+        },
+        [&](int64_t i) { x[i] *= s; });
 }
 
 void launch_scale_inv_norm(float* x, int64_t n, const double* acc, int* flags, cudaStream_t s) {
     int blocks = (int)((n + 255) / 256);
     if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
-    scale_inv_norm_kernel<<<blocks, 256, 0, s>>>(x, n, acc, flags); count_launches(1);
+    scale_inv_norm_kernel<<<blocks, 256, 0, s>>>(x, n, aligned16(x), acc, flags); count_launches(1);
 }
 
-__global__ void dot2_kernel(const float* x, const float* y, int64_t n, double* acc) {
+__global__ void dot2_kernel(const float* x, const float* y, int64_t n, bool vec, double* acc) {
     float a = 0.f, b = 0.f;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        a += x[i] * y[i];
-        b += x[i] * x[i];
-    }
+    for_each_flat(
+        n, vec,
+        [&](int64_t i) {
+            const float4 p = reinterpret_cast<const float4*>(x)[i], q = reinterpret_cast<const float4*>(y)[i];
+            a += p.x * q.x + p.y * q.y + p.z * q.z + p.w * q.w;
+            b += p.x * p.x + p.y * p.y + p.z * p.z + p.w * p.w;
+        },
+        [&](int64_t i) {
+            a += x[i] * y[i];
+            b += x[i] * x[i];
+        });
     const double sa = block_sum((double)a);
     if (threadIdx.x == 0) atomicAdd(acc, sa);
     const double sb = block_sum((double)b);
     if (threadIdx.x == 0) atomicAdd(acc + 1, sb);
 }
 
-__global__ void resid_kernel(const float* x, const float* y, int64_t n, double* acc) {
+__global__ void resid_kernel(const float* x, const float* y, int64_t n, bool vec, double* acc) {
     const float rho = (float)(acc[0] / acc[1]);
     float a = 0.f;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const float d = y[i] - rho * x[i];
-        a += d * d;
-    }
+    for_each_flat(
+        n, vec,
+        [&](int64_t i) {
+            const float4 p = reinterpret_cast<const float4*>(x)[i], q = reinterpret_cast<const float4*>(y)[i];
+            const float d0 = q.x - rho * p.x, d1 = q.y - rho * p.y, d2 = q.z - rho * p.z, d3 = q.w - rho * p.w;
+            a += d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3;
+        },
+        [&](int64_t i) {
+            const float d = y[i] - rho * x[i];
+            a += d * d;
+        });
     const double sa = block_sum((double)a);
     if (threadIdx.x == 0) atomicAdd(acc + 2, sa);
 }
 
-__global__ void sumsq_kernel(const float* x, int64_t n, double* acc) {
+__global__ void sumsq_kernel(const float* x, int64_t n, bool vec, double* acc) {
     float a = 0.f;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        a = fmaf(x[i], x[i], a);
+    for_each_flat(
+        n, vec,
+        [&](int64_t i) {
+            const float4 p = reinterpret_cast<const float4*>(x)[i];
+            a = fmaf(p.x, p.x, fmaf(p.y, p.y, fmaf(p.z, p.z, fmaf(p.w, p.w, a))));
+        },
+        [&](int64_t i) { a = fmaf(x[i], x[i], a); });
     const double sa = block_sum((double)a);
     if (threadIdx.x == 0) atomicAdd(acc, sa);
 }
@@ -353,19 +378,19 @@ void launch_sumsq(const float* x, int64_t n, double* acc, cudaStream_t s) {
     int blocks = (int)((n + 255) / 256);
     if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
     if (blocks < 1) blocks = 1;
-    sumsq_kernel<<<blocks, 256, 0, s>>>(x, n, acc); count_launches(1);
+    sumsq_kernel<<<blocks, 256, 0, s>>>(x, n, aligned16(x), acc); count_launches(1);
 }
 
 void launch_dot2(const float* x, const float* y, int64_t n, double* acc, cudaStream_t s) {
     int blocks = (int)((n + 255) / 256);
     if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
-    dot2_kernel<<<blocks, 256, 0, s>>>(x, y, n, acc); count_launches(1);
+    dot2_kernel<<<blocks, 256, 0, s>>>(x, y, n, aligned16(x, y), acc); count_launches(1);
 }
 
 void launch_resid(const float* x, const float* y, int64_t n, double* acc, cudaStream_t s) {
     int blocks = (int)((n + 255) / 256);
     if (blocks > 8 * num_sms()) blocks = 8 * num_sms();
-    resid_kernel<<<blocks, 256, 0, s>>>(x, y, n, acc); count_launches(1);
+    resid_kernel<<<blocks, 256, 0, s>>>(x, y, n, aligned16(x, y), acc); count_launches(1);
 }
 
 }  // namespace sfseg

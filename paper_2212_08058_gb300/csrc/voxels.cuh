@@ -18,6 +18,26 @@ __device__ __forceinline__ void for_each_voxel(const Geom& g, F&& f) {
     }
 }
 
+// f4(i) for the groups [4i, 4i + 4) of [0, n) and f1(i) for the n % 4 elements after them when
+// vec (every array the caller touches is 16-byte aligned), else f1(i) for every element: the
+// flat element-wise passes then move 16 bytes per access.
+template <typename F4, typename F1>
+__device__ __forceinline__ void for_each_flat(int64_t n, bool vec, F4&& f4, F1&& f1) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t first = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t done = 0;
+    if (vec) {
+        const int64_t n4 = n >> 2;
+        for (int64_t i = first; i < n4; i += stride) f4(i);
+        done = n4 << 2;
+    }
+    for (int64_t i = done + first; i < n; i += stride) f1(i);
+}
+
+inline bool aligned16(const void* a, const void* b = nullptr) {
+    return (((uintptr_t)a | (uintptr_t)b) & 15) == 0;
+}
+
 // Launch shape for for_each_voxel: up to 256 threads (a multiple of 32 covering W when W is
 // small), at most `per_sm` blocks per SM.
 struct RowLaunch {
