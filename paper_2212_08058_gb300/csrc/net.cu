@@ -12,10 +12,12 @@
 //   C_in/16 MMAs each carry the three taps along h at once (N = 3 x output channels, D over the
 //   accumulators of the three output rows it feeds, a ring of blocks in TMEM).
 // The A operand is read straight from a TMA-filled ring of input rows in the canonical
-// no-swizzle K-major layout ([8-channel chunk][3 frames][130 voxels][8 channels]); a tap's shift
+// no-swizzle K-major layout ([8-channel chunk][frames][130 voxels][8 channels]); a tap's shift
 // along w is a 16-byte offset of the descriptor's start address, along t a 2080-byte offset.
-// All weights of the layer stay in shared memory.  One warp issues the TMA copies, one the MMAs,
-// four read each finished row's accumulator from TMEM, zero it, and run the epilogue.  The
+// All weights of the layer stay in shared memory.  A CTA computes two consecutive output frames
+// from input slots of four frames: one warp issues the TMA copies, two issue the MMAs (one per
+// output frame, each into its half of TMEM), eight (four per frame) read each finished row's
+// accumulator from TMEM, zero it, and run the epilogue.  The
 // backward pass reuses the same kernel for the data gradient (flipped taps, transposed
 // channels, ReLU mask in the epilogue); the weight gradient is its own tcgen05 kernel with the
 // voxels as the reduction dimension (wgrad_tc).
@@ -42,6 +44,13 @@ constexpr int CHUNK_BYTES = (CHUNK_DATA + 127) / 128 * 128;   // its stride (128
 #endif
 constexpr int NSLOT = SFSEG_NET_NSLOT;  // input-row ring (rows in flight ahead of the MMAs: NSLOT - 2)
 constexpr int NTHR = 192;               // 6 warps
+// Output frames per CTA of conv3d_tc, one MMA-issuing thread each.  A thread issues tcgen05.mma
+// at most about once per 150 clocks whatever the instruction's N (measured), so at N = 96 one
+// issuer keeps the tensor pipe about a third busy; two frames per CTA give the SM two issuers,
+// which share each loaded input row (four frames of it instead of three per output frame).
+#ifndef SFSEG_NET_CONV_FR
+#define SFSEG_NET_CONV_FR 2
+#endif
 // Output rows per CTA: the tallest of 64, 32, 16 that still gives the grid 4 waves (taller
 // tiles load fewer halo rows and amortise each CTA's weight copy and TMEM set-up).
 constexpr int kHrChoices[3] = {64, 32, 16};
@@ -176,71 +185,83 @@ struct ConvArgs {
 
 // The three taps along h of one (dt, dw, ks) share one MMA: an input row h' feeds the output
 // rows h' + 1, h', h' - 1 through the weights of dh = 0, 1, 2, so B stacks the three weight
-// blocks along N (N = 3 COUT) and D spans the accumulators of three output rows.  The
-// accumulators form a ring of R blocks of COUT columns over all 512 TMEM columns; output row j
-// uses block (-j) mod R, so the rows i, i - 1, i - 2 fed by input row i sit in consecutive
-// blocks (an MMA is split in two where the ring wraps, and trimmed at the tile's first and last
-// rows).  A block is zeroed when its row has been read, so every MMA accumulates.
+// blocks along N (N = 3 COUT) and D spans the accumulators of three output rows.  Each output
+// frame of the CTA has a ring of R blocks of COUT columns in its half of the TMEM columns;
+// output row j uses block (-j) mod R, so the rows i, i - 1, i - 2 fed by input row i sit in
+// consecutive blocks (an MMA is split in two where the ring wraps, and trimmed at the tile's
+// first and last rows).  A block is zeroed when its row has been read, so every MMA accumulates.
+// An input slot holds FR + 2 frames of one row; the issuer of output frame t0 + q reads its
+// frames q, q + 1, q + 2.
 template <int CIN, int COUT>
 struct ConvCfg {
+    static constexpr int FR = SFSEG_NET_CONV_FR;              // output frames per CTA
+    static constexpr int NF = FR + 2;                         // frames per input slot
     static constexpr int NCH = CIN / 8;                       // 8-channel chunks of A
     static constexpr int KS = CIN / 16;                       // MMAs per tap
-    static constexpr int SLOT_BYTES = NCH * CHUNK_BYTES;
+    static constexpr int CHUNK_DATA = NF * RW * 16;           // one 8-channel chunk of NF frames
+    static constexpr int CHUNK = (CHUNK_DATA + 127) / 128 * 128;   // its stride (128-byte aligned TMA target)
+    static constexpr int SLOT_BYTES = NCH * CHUNK;
     static constexpr int WBYTES = 27 * KS * 2 * COUT * 16;    // packed weights
-    static constexpr int TMEM_COLS = 512;
-    static constexpr int R = TMEM_COLS / COUT;                // accumulator blocks in the ring
-    static constexpr int NB = 2 * NSLOT + 2 * R + 2;          // full, empty, accf[R], acce[R], wbar, drain
+    static constexpr int RING = 512 / FR;                     // TMEM columns of one output frame
+    static constexpr int R = RING / COUT;                     // accumulator blocks in its ring
+    static constexpr int NS = 4;                              // input-row slots
+    static constexpr int NTHR = 32 * (1 + FR + 4 * FR);       // producer, issuers, 4 epilogue warps per frame
+    // full[NS], empty[NS], accf[FR][R], acce[FR][R], wbar, drain[FR]
+    static constexpr int NB = 2 * NS + 2 * FR * R + 1 + FR;
+    static constexpr int SMEM_NEED = WBYTES + NS * SLOT_BYTES + NB * 8 + 16 + 128;
     // at least 120 KB so that one CTA holds the SM's tensor memory alone
-    static constexpr int SMEM_NEED = WBYTES + NSLOT * SLOT_BYTES + NB * 8 + 16 + 128;
     static constexpr int SMEM = SMEM_NEED > 120 * 1024 ? SMEM_NEED : 120 * 1024;
+    static_assert(FR == 1 || FR == 2, "one or two output frames per CTA");
     static_assert(R >= 4 && 3 * COUT <= 256 && COUT % 16 == 0, "accumulator ring");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
 template <int CIN, int COUT, int EPI>
-__global__ void __launch_bounds__(NTHR, 1)
+__global__ void __launch_bounds__(ConvCfg<CIN, COUT>::NTHR, 1)
 conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
     using C = ConvCfg<CIN, COUT>;
     extern __shared__ __align__(128) unsigned char sm_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)sm_raw + 127) & ~(uintptr_t)127);
     unsigned char* wsm = sm;                                   // weights
-    unsigned char* ring = sm + C::WBYTES;                      // NSLOT input rows
-    uint64_t* bar = reinterpret_cast<uint64_t*>(ring + NSLOT * C::SLOT_BYTES);
-    uint64_t* full = bar;                        // [NSLOT]
-    uint64_t* empty = bar + NSLOT;               // [NSLOT]
-    uint64_t* accf = bar + 2 * NSLOT;            // [R]: the row in accumulator block b is complete
-    uint64_t* acce = bar + 2 * NSLOT + C::R;     // [R]: block b has been read and zeroed
-    uint64_t* wbar = bar + 2 * NSLOT + 2 * C::R;
-    uint64_t* drain = wbar + 1;                  // completion of this CTA's MMAs, awaited after a timeout
+    unsigned char* ring = sm + C::WBYTES;                      // the input-row slots
+    uint64_t* bar = reinterpret_cast<uint64_t*>(ring + C::NS * C::SLOT_BYTES);
+    uint64_t* full = bar;                        // [NS]
+    uint64_t* empty = bar + C::NS;               // [NS]: released by each active issuer
+    uint64_t* accf = bar + 2 * C::NS;            // [FR][R]: the row in accumulator block b is complete
+    uint64_t* acce = accf + C::FR * C::R;        // [FR][R]: block b has been read and zeroed
+    uint64_t* wbar = acce + C::FR * C::R;
+    uint64_t* drain = wbar + 1;                  // [FR]: completion of an issuer's MMAs, awaited after a timeout
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + C::NB);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // work item: (t, w segment, row range)
+    // work item: (pair of frames, w segment, row range)
     const int HR = a.HR;
     const int nws = (a.W + MT - 1) / MT, nhr = (a.H + HR - 1) / HR;
     int item = blockIdx.x;
     const int hr = item % nhr;
     item /= nhr;
     const int ws = item % nws;
-    const int t = item / nws;
+    const int t0 = (item / nws) * C::FR;
+    const int nfr = min(C::FR, a.T - t0);        // output frames of this CTA (1 at an odd T's end)
     const int w0 = ws * MT, hs = hr * HR, he = min(a.H, hs + HR);
     const int nout = he - hs, nin = nout + 2;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < NSLOT; ++i) {
+        for (int i = 0; i < C::NS; ++i) {
             mb_init(&full[i], 1);
-            mb_init(&empty[i], 1);
+            mb_init(&empty[i], (uint32_t)nfr);
         }
-        for (int i = 0; i < C::R; ++i) {
+        for (int i = 0; i < C::FR * C::R; ++i) {
             mb_init(&accf[i], 1);
             mb_init(&acce[i], 4);
         }
         mb_init(wbar, 1);
-        mb_init(drain, 1);
+        for (int q = 0; q < C::FR; ++q) mb_init(&drain[q], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                     "r"(C::TMEM_COLS)
+                     "r"(512)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -249,10 +270,11 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     auto blk = [&](int j) { return (C::R - j % C::R) % C::R; };   // accumulator block of output row j
-    if (warp >= 2) {   // the epilogue warps zero the whole ring (their lane quadrants) once
-        const uint32_t lanes = (uint32_t)((warp & 3) * 32) << 16;
+    const int epi = warp - 1 - C::FR;            // epilogue warp index, 4 per output frame
+    if (epi >= 0) {   // the epilogue warps zero their frame's ring (their lane quadrants) once
+        const uint32_t base = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((epi >> 2) * C::RING);
 #pragma unroll 1
-        for (int b = 0; b < C::R; ++b) tmem_zero<COUT>(tmem + lanes + (uint32_t)(b * COUT));
+        for (int b = 0; b < C::R; ++b) tmem_zero<COUT>(base + (uint32_t)(b * COUT));
         tmem_st_wait();
     }
     tc_fence_before();
@@ -265,57 +287,78 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
             mb_expect(wbar, C::WBYTES);
             bulk_g2s(wsm, a.wpack, C::WBYTES, wbar);
             for (int i = 0; i < nin; ++i) {
-                const int s = i % NSLOT;
-                if (i >= NSLOT && !mb_wait(&empty[s], (uint32_t)((i / NSLOT - 1) & 1), a.flags)) break;
+                const int s = i % C::NS;
+                if (i >= C::NS && !mb_wait(&empty[s], (uint32_t)((i / C::NS - 1) & 1), a.flags)) break;
                 issued = i + 1;
-                mb_expect(&full[s], C::NCH * CHUNK_DATA);
+                mb_expect(&full[s], C::NCH * C::CHUNK_DATA);
                 unsigned char* dst = ring + s * C::SLOT_BYTES;
-                for (int k = 0; k < C::NCH; ++k) tma4(dst + k * CHUNK_BYTES, &xin, &full[s], 8 * k, w0 - 1, hs - 1 + i, t - 1);
+                for (int k = 0; k < C::NCH; ++k) tma4(dst + k * C::CHUNK, &xin, &full[s], 8 * k, w0 - 1, hs - 1 + i, t0 - 1);
             }
         }
-    } else if (warp == 1) {
-        if (lane == 0) {   // ---------------- MMA issuer: one group of MMAs per input row
+    } else if (epi < 0) {
+        const int q = warp - 1;      // output frame t0 + q
+        if (lane == 0 && q < nfr) {   // ---------------- MMA issuer of one output frame
             bool ok = mb_wait(wbar, 0, a.flags);
             const uint32_t wbase = su32(wsm), rbase = su32(ring);
+            const uint32_t dbase = tmem + (uint32_t)(q * C::RING);
+            uint64_t* af = accf + q * C::R;
+            uint64_t* ae = acce + q * C::R;
             constexpr uint32_t TILE = 2 * 3 * COUT * 16;          // stacked B tile of one (dt, dw, ks)
             for (int i = 0; ok && i < nin; ++i) {
-                ok = mb_wait(&full[i % NSLOT], (uint32_t)((i / NSLOT) & 1), a.flags);
+                ok = mb_wait(&full[i % C::NS], (uint32_t)((i / C::NS) & 1), a.flags);
                 // output rows fed by input row i: j = i - dh for dh = 0, 1, 2, within [0, nout)
                 const int jhi = min(i, nout - 1), jlo = max(i - 2, 0);
                 // row i enters the ring: its block must have been read back from row i - R
                 if (ok && i < nout && i >= C::R)
-                    ok = mb_wait(&acce[blk(i)], (uint32_t)(((i - C::R) / C::R) & 1), a.flags);
+                    ok = mb_wait(&ae[blk(i)], (uint32_t)(((i - C::R) / C::R) & 1), a.flags);
                 if (!ok) break;
                 tc_fence_after();
                 const int dh0 = i - jhi, nrow = jhi - jlo + 1;
                 const int b0 = blk(jhi);
                 const int n1 = min(nrow, C::R - b0), n2 = nrow - n1;   // before and after the wrap
                 const uint32_t id1 = idesc_bf16(n1 * COUT), id2 = idesc_bf16((n2 > 0 ? n2 : 1) * COUT);
-                const uint32_t d1 = tmem + (uint32_t)(b0 * COUT), d2 = tmem;
-                const uint64_t a0 = sdesc(rbase + (uint32_t)((i % NSLOT) * C::SLOT_BYTES), CHUNK_BYTES, 128);
+                const uint32_t d1 = dbase + (uint32_t)(b0 * COUT), d2 = dbase;
+                const uint64_t a0 = sdesc(rbase + (uint32_t)((i % C::NS) * C::SLOT_BYTES + q * RW * 16), C::CHUNK, 128);
                 // B of rows dh0 .. and of the rows after the wrap: same tiles, later start rows
                 const uint64_t bA = sdesc(wbase + (uint32_t)(dh0 * COUT * 16), 3 * COUT * 16, 128);
                 const uint64_t bB = sdesc(wbase + (uint32_t)((dh0 + n1) * COUT * 16), 3 * COUT * 16, 128);
+                // The row's MMAs as one branch-free run, then those of the rows after the wrap as a
+                // second: a conditional MMA between consecutive ones halved the issue rate (measured).
+                // Each accumulator block still receives its contributions in the same order.
 #pragma unroll
                 for (int dt = 0; dt < 3; ++dt)
 #pragma unroll
-                    for (int dw = 0; dw < 3; ++dw) {
+                    for (int dw = 0; dw < 3; ++dw)
 #pragma unroll
                         for (int ks = 0; ks < C::KS; ++ks) {
-                            const uint64_t ad = a0 + (uint64_t)((2 * ks * CHUNK_BYTES + dt * RW * 16 + dw * 16) >> 4);
+                            const uint64_t ad = a0 + (uint64_t)((2 * ks * C::CHUNK + dt * RW * 16 + dw * 16) >> 4);
                             const uint64_t toff = (uint64_t)((((dt * 3 + dw) * C::KS + ks) * TILE) >> 4);
                             umma(d1, ad, bA + toff, id1, 1u);
-                            if (n2 > 0) umma(d2, ad, bB + toff, id2, 1u);
                         }
-                    }
-                umma_commit(&empty[i % NSLOT]);
-                if (i >= 2 && i - 2 < nout) umma_commit(&accf[blk(i - 2)]);
+                if (n2 > 0) {
+#pragma unroll
+                    for (int dt = 0; dt < 3; ++dt)
+#pragma unroll
+                        for (int dw = 0; dw < 3; ++dw)
+#pragma unroll
+                            for (int ks = 0; ks < C::KS; ++ks) {
+                                const uint64_t ad = a0 + (uint64_t)((2 * ks * C::CHUNK + dt * RW * 16 + dw * 16) >> 4);
+                                const uint64_t toff = (uint64_t)((((dt * 3 + dw) * C::KS + ks) * TILE) >> 4);
+                                umma(d2, ad, bB + toff, id2, 1u);
+                            }
+                }
+                umma_commit(&empty[i % C::NS]);
+                if (i >= 2 && i - 2 < nout) umma_commit(&af[blk(i - 2)]);
             }
         }
-    } else {   // ---------------- epilogue: warps 2..5
-        const int q = warp & 3;          // TMEM lane quadrant of this warp
-        const int v = q * 32 + lane;     // voxel within the tile
+    } else if ((epi >> 2) < nfr) {   // ---------------- epilogue: 4 warps per output frame
+        const int f = epi >> 2;          // output frame t0 + f
+        const int qd = warp & 3;         // TMEM lane quadrant of this warp
+        const int v = qd * 32 + lane;    // voxel within the tile
         const int w = w0 + v;
+        const int t = t0 + f;
+        uint64_t* af = accf + f * C::R;
+        uint64_t* ae = acce + f * C::R;
         // the bias in registers, read once (the output stores may alias it as far as the compiler
         // knows, which would otherwise reload it for every row)
         float bz[EPI == EPI_RELU ? COUT : 1];
@@ -323,17 +366,17 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
         for (int c = 0; c < (int)(sizeof(bz) / sizeof(float)); ++c) bz[c] = EPI == EPI_MASK ? 0.f : a.bias[c];
         for (int j = 0; j < nout; ++j) {
             const int b = blk(j);
-            const bool ok = mb_wait(&accf[b], (uint32_t)((j / C::R) & 1), a.flags);
+            const bool ok = mb_wait(&af[b], (uint32_t)((j / C::R) & 1), a.flags);
             tc_fence_after();
             uint32_t r[COUT];
-            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * COUT);
+            const uint32_t taddr = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(f * C::RING + b * COUT);
             tmem_ld<COUT>(taddr, r);
             tmem_ld_wait();
             tmem_zero<COUT>(taddr);      // the block's next row accumulates from zero
             tmem_st_wait();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mb_arrive(&acce[b]);
+            if (lane == 0) mb_arrive(&ae[b]);
             if (!ok) break;
             const int h = hs + j;
             if (w >= a.W) continue;
@@ -375,19 +418,18 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
         // in flight land before its shared memory and TMEM are released.  Each wait is bounded.
         if (warp == 0 && lane == 0) {
             mb_settle(wbar, 0);
-            for (int s = 0; s < NSLOT && s < issued; ++s) {
-                const int last = s + ((issued - 1 - s) / NSLOT) * NSLOT;
-                mb_settle(&full[s], (uint32_t)((last / NSLOT) & 1));
+            for (int s = 0; s < C::NS && s < issued; ++s) {
+                const int last = s + ((issued - 1 - s) / C::NS) * C::NS;
+                mb_settle(&full[s], (uint32_t)((last / C::NS) & 1));
             }
-        } else if (warp == 1 && lane == 0) {
-            umma_commit(drain);      // arrives when every MMA this thread issued has completed
-            mb_settle(drain, 0);
+        } else if (epi < 0 && lane == 0 && warp - 1 < nfr) {
+            umma_commit(&drain[warp - 1]);   // arrives when every MMA this thread issued has completed
+            mb_settle(&drain[warp - 1], 0);
         }
         __syncthreads();
     }
     tc_fence_after();
-    if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(C::TMEM_COLS) : "memory");
+    if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
 }
 
 // -------------------------------------------------------------- last layer (32 -> 1, tcgen05)
@@ -920,12 +962,12 @@ EncodeFn encode() {
 
 // 4D map over a channels-last bf16 activation [T][H][W][C]; box = 8 channels x 130 voxels x
 // 1 row x 3 frames (one A chunk of one input row).
-bool act_map(CUtensorMap* m, const void* base, int C, int T, int H, int W) {
+bool act_map(CUtensorMap* m, const void* base, int C, int T, int H, int W, int frames = 3) {
     EncodeFn fn = encode();
     if (!fn) return false;
     cuuint64_t dims[4] = {(cuuint64_t)C, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)T};
     cuuint64_t str[3] = {(cuuint64_t)C * 2, (cuuint64_t)C * 2 * W, (cuuint64_t)C * 2 * W * H};
-    cuuint32_t box[4] = {8, (cuuint32_t)RW, 1, 3};
+    cuuint32_t box[4] = {8, (cuuint32_t)RW, 1, (cuuint32_t)frames};
     cuuint32_t es[4] = {1, 1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(base), dims, str, box, es,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -1020,7 +1062,7 @@ int run_conv(const void* in, int T, int H, int W, const __nv_bfloat16* wpack, co
              const __nv_bfloat16* mask, int* flags, cudaStream_t s) {
     using Cf = ConvCfg<CIN, COUT>;
     CUtensorMap m;
-    if (!act_map(&m, in, CIN, T, H, W)) return nfail(SFSEG_ERR_CUDA, "tensor map encoding failed");
+    if (!act_map(&m, in, CIN, T, H, W, Cf::NF)) return nfail(SFSEG_ERR_CUDA, "tensor map encoding failed");
     auto k = conv3d_tc<CIN, COUT, EPI>;
     static bool attr = false;
     if (!attr) {
@@ -1033,10 +1075,10 @@ int run_conv(const void* in, int T, int H, int W, const __nv_bfloat16* wpack, co
     int items = 0;
     for (int hr : kHrChoices) {
         a.HR = hr;
-        items = T * ((W + MT - 1) / MT) * ((H + hr - 1) / hr);
+        items = (T + Cf::FR - 1) / Cf::FR * ((W + MT - 1) / MT) * ((H + hr - 1) / hr);
         if (items >= 4 * num_sms()) break;
     }
-    k<<<items, NTHR, Cf::SMEM, s>>>(m, a);
+    k<<<items, Cf::NTHR, Cf::SMEM, s>>>(m, a);
     count_launches(1);
     NET_CUDA(cudaGetLastError());
     return SFSEG_OK;
