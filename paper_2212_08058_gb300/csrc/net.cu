@@ -44,13 +44,6 @@ constexpr int CHUNK_BYTES = (CHUNK_DATA + 127) / 128 * 128;   // its stride (128
 #endif
 constexpr int NSLOT = SFSEG_NET_NSLOT;  // input-row ring (rows in flight ahead of the MMAs: NSLOT - 2)
 constexpr int NTHR = 192;               // 6 warps
-// Output frames per CTA of conv3d_tc, one MMA-issuing thread each.  A thread issues tcgen05.mma
-// at most about once per 150 clocks whatever the instruction's N (measured), so at N = 96 one
-// issuer keeps the tensor pipe about a third busy; two frames per CTA give the SM two issuers,
-// which share each loaded input row (four frames of it instead of three per output frame).
-#ifndef SFSEG_NET_CONV_FR
-#define SFSEG_NET_CONV_FR 2
-#endif
 // Output rows per CTA: the tallest of 64, 32, 16 that still gives the grid 4 waves (taller
 // tiles load fewer halo rows and amortise each CTA's weight copy and TMEM set-up).
 constexpr int kHrChoices[3] = {64, 32, 16};
@@ -192,9 +185,13 @@ struct ConvArgs {
 // first and last rows).  A block is zeroed when its row has been read, so every MMA accumulates.
 // An input slot holds FR + 2 frames of one row; the issuer of output frame t0 + q reads its
 // frames q, q + 1, q + 2.
-template <int CIN, int COUT>
+// FR output frames per CTA, one MMA-issuing thread each: two issuers keep the tensor pipe busier
+// than one (each waits on its own barriers and its MMAs' operand reads), and the two frames share
+// each loaded input row (four frames of it instead of three per output frame).  One frame per
+// CTA serves volumes too small to fill the GPU with two.
+template <int CIN, int COUT, int FR_>
 struct ConvCfg {
-    static constexpr int FR = SFSEG_NET_CONV_FR;              // output frames per CTA
+    static constexpr int FR = FR_;                            // output frames per CTA
     static constexpr int NF = FR + 2;                         // frames per input slot
     static constexpr int NCH = CIN / 8;                       // 8-channel chunks of A
     static constexpr int KS = CIN / 16;                       // MMAs per tap
@@ -216,10 +213,10 @@ struct ConvCfg {
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
-template <int CIN, int COUT, int EPI>
-__global__ void __launch_bounds__(ConvCfg<CIN, COUT>::NTHR, 1)
+template <int CIN, int COUT, int EPI, int FR>
+__global__ void __launch_bounds__(ConvCfg<CIN, COUT, FR>::NTHR, 1)
 conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
-    using C = ConvCfg<CIN, COUT>;
+    using C = ConvCfg<CIN, COUT, FR>;
     extern __shared__ __align__(128) unsigned char sm_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)sm_raw + 127) & ~(uintptr_t)127);
     unsigned char* wsm = sm;                                   // weights
@@ -1057,31 +1054,49 @@ int ensure_ws(sfseg_net* n, int64_t N, bool train) {
     return SFSEG_OK;
 }
 
-template <int CIN, int COUT, int EPI>
-int run_conv(const void* in, int T, int H, int W, const __nv_bfloat16* wpack, const float* bias, void* out,
-             const __nv_bfloat16* mask, int* flags, cudaStream_t s) {
-    using Cf = ConvCfg<CIN, COUT>;
+template <int CIN, int COUT, int EPI, int FR>
+int launch_conv(const void* in, int T, int H, int W, const ConvArgs& a, int items, cudaStream_t s) {
+    using Cf = ConvCfg<CIN, COUT, FR>;
     CUtensorMap m;
     if (!act_map(&m, in, CIN, T, H, W, Cf::NF)) return nfail(SFSEG_ERR_CUDA, "tensor map encoding failed");
-    auto k = conv3d_tc<CIN, COUT, EPI>;
+    auto k = conv3d_tc<CIN, COUT, EPI, FR>;
     static bool attr = false;
     if (!attr) {
         NET_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM));
         attr = true;
     }
-    ConvArgs a;
-    a.T = T; a.H = H; a.W = W;
-    a.wpack = wpack; a.bias = bias; a.out = out; a.mask = mask; a.flags = flags;
-    int items = 0;
-    for (int hr : kHrChoices) {
-        a.HR = hr;
-        items = (T + Cf::FR - 1) / Cf::FR * ((W + MT - 1) / MT) * ((H + hr - 1) / hr);
-        if (items >= 4 * num_sms()) break;
-    }
     k<<<items, Cf::NTHR, Cf::SMEM, s>>>(m, a);
     count_launches(1);
     NET_CUDA(cudaGetLastError());
     return SFSEG_OK;
+}
+
+// Two output frames per CTA when that grid still gives 4 waves at some tile height, else one;
+// then the tallest tile of 64, 32, 16 output rows that gives 4 waves (taller tiles load fewer
+// halo rows and amortise each CTA's weight copy and TMEM set-up).
+template <int CIN, int COUT, int EPI>
+int run_conv(const void* in, int T, int H, int W, const __nv_bfloat16* wpack, const float* bias, void* out,
+             const __nv_bfloat16* mask, int* flags, cudaStream_t s) {
+    ConvArgs a;
+    a.T = T; a.H = H; a.W = W;
+    a.wpack = wpack; a.bias = bias; a.out = out; a.mask = mask; a.flags = flags;
+    const int nws = (W + MT - 1) / MT;
+    int fr = 1, items = 0;
+    a.HR = kHrChoices[2];
+    for (int f : {2, 1}) {
+        bool found = false;
+        for (int hr : kHrChoices) {
+            const int n = (T + f - 1) / f * nws * ((H + hr - 1) / hr);
+            if (n >= 4 * num_sms()) {
+                fr = f, a.HR = hr, items = n, found = true;
+                break;
+            }
+        }
+        if (found) break;
+    }
+    if (items == 0) items = T * nws * ((H + a.HR - 1) / a.HR);   // small volume: one frame, 16 rows
+    return fr == 2 ? launch_conv<CIN, COUT, EPI, 2>(in, T, H, W, a, items, s)
+                   : launch_conv<CIN, COUT, EPI, 1>(in, T, H, W, a, items, s);
 }
 
 // The last layer (32 -> 1) on its own kernel, 126-voxel tiles along w (conv_last_tc).

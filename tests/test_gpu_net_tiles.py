@@ -35,16 +35,16 @@ def sf():
     return sfseg
 
 
-FRAMES_PER_CTA = 2      # output frames of one convolution CTA (two MMA issuers)
-
-
-def _tile_rows(T, H, W):
-    """The row count per CTA the convolution launch picks for this volume (see net.cu)."""
+def _conv_launch(T, H, W):
+    """(output frames, output rows) per CTA that the convolution launch picks for this volume
+    (see net.cu): two frames when that grid still gives 4 waves at some tile height, else one."""
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
-    for hr in (64, 32, 16):
-        if -(-T // FRAMES_PER_CTA) * -(-W // 128) * -(-H // hr) >= 4 * nsm:
-            return hr
-    return 16
+    for fr in (2, 1):
+        for hr in (64, 32, 16):
+            if -(-T // fr) * -(-W // 128) * -(-H // hr) >= 4 * nsm:
+                return fr, hr
+    return 1, 16
+
 
 
 def _points(T, H, W, HR, seed, n_random=40):
@@ -133,16 +133,17 @@ def _last_layer_rows(T, H, W):
     return 16
 
 
-@pytest.mark.parametrize("shape,hr,hr_last", [((17, 1024, 640), 64, 64), ((8, 1024, 640), 32, 32),
-                                             ((32, 256, 512), 16, 32)],
-                         ids=["rows64_odd_frames", "rows32", "rows16"])
-def test_layers_at_production_tile_heights(sf, shape, hr, hr_last):
+@pytest.mark.parametrize("shape,fr,hr,hr_last", [((17, 1024, 640), 2, 64, 64), ((8, 1024, 640), 2, 32, 32),
+                                                ((32, 256, 512), 2, 16, 32), ((2, 1024, 640), 1, 16, 16)],
+                         ids=["rows64_odd_frames", "rows32", "rows16", "one_frame_per_cta"])
+def test_layers_at_production_tile_heights(sf, shape, fr, hr, hr_last):
     """Each layer's output at sampled voxels against the oracle's convolution of the GPU layer's
-    own input, at the tile height the launch picks for this volume (the last layer's kernel
-    picks its own, 64 rows as at 1080p for the first volume).  With 17 frames the last CTA of
-    each hidden layer computes one output frame instead of two."""
+    own input, at the frames and tile height per CTA the launch picks for this volume (the last
+    layer's kernel picks its own, 64 rows as at 1080p for the first volume).  With 17 frames the
+    last CTA of each hidden layer computes one output frame instead of two; the 2-frame volume
+    runs one output frame per CTA."""
     T, H, W = shape
-    assert _tile_rows(T, H, W) == hr
+    assert _conv_launch(T, H, W) == (fr, hr)
     assert _last_layer_rows(T, H, W) == hr_last
     net = sf.WarmStartNet(C_IN, seed=11)
     params = _layer_params(net)
@@ -164,7 +165,7 @@ def test_data_gradient_at_production_tile_heights(sf, shape, hr):
     """dx = conv^T(dz) * [x > 0] of layers 1..3 (the data-gradient convolution on the tensor
     cores) at sampled voxels against the oracle's reverse loops on the same bf16 inputs."""
     T, H, W = shape
-    assert _tile_rows(T, H, W) == hr
+    assert _conv_launch(T, H, W) == (2, hr)
     net = sf.WarmStartNet(C_IN, seed=12)
     params = _layer_params(net)
     ins, _, _ = _forward_layers(net, _input16(T, H, W, 910 + hr))
@@ -255,7 +256,7 @@ def test_network_sampled_at_production_tile_heights(sf, shape, hr):
     oracle's FP64 network on the 9 x 9 x 9 crop around each voxel, within the end-to-end bf16
     tolerance of the small network test (three hidden activations rounded to bf16)."""
     T, H, W = shape
-    assert _tile_rows(T, H, W) == hr
+    assert _conv_launch(T, H, W) == (2, hr)
     gen = torch.Generator(device="cuda").manual_seed(940 + hr)
     feats = torch.rand((8, T, H, W), device="cuda", generator=gen).to(torch.bfloat16)
     extra = torch.rand((T, H, W), device="cuda", generator=gen)
