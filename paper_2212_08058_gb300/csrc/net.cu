@@ -37,8 +37,6 @@ namespace net {
 
 constexpr int MT = 128;                 // voxels per MMA tile (rows of A)
 constexpr int RW = MT + 2;              // voxels per loaded row (w halo of 1)
-constexpr int CHUNK_DATA = 3 * RW * 16;    // one 8-channel chunk of 3 frames: 6240 B
-constexpr int CHUNK_BYTES = (CHUNK_DATA + 127) / 128 * 128;   // its stride (128-byte aligned TMA target)
 #ifndef SFSEG_NET_NSLOT
 #define SFSEG_NET_NSLOT 4
 #endif
@@ -441,9 +439,6 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
 // neighbours along w may sit in another warp) and adds them.  M = 128 voxels cover 126 outputs
 // and their w halo, so the tiles are 126 voxels wide.
 constexpr int LT_W = MT - 2;                 // outputs per tile along w
-constexpr int LT_R = 16;                     // TMEM blocks (input rows) in the ring
-constexpr int LT_COLS = LT_R * 16;           // 256: two CTAs can share an SM's tensor memory
-constexpr int LT_SLOT = 4 * CHUNK_BYTES;     // one input row: 4 chunks of 8 channels x 3 frames
 constexpr int LT_BBYTES = 3 * 2 * 2 * 16 * 16;   // [dt][ks][chunk][16 taps][8 channels] bf16
 
 struct LastArgs {
@@ -455,28 +450,49 @@ struct LastArgs {
     int* flags;
 };
 
+// FR output frames per CTA from input slots of FR + 2 frames (each output frame reads three of
+// them): the input bytes copied per output voxel fall from 3 x 64 to (FR + 2) / FR x 64.  Each
+// output frame has its own ring of R TMEM blocks, one per input row, and its own four epilogue
+// warps.  One frame per CTA (a ring of 16 blocks in 256 columns, two CTAs per SM) serves volumes
+// too small for the four-frame grid.
+template <int FR>
 struct LastCfg {
-    static constexpr int NB = 2 * NSLOT + 2 * LT_R + 2;
-    static constexpr int XS = 2 * 3 * 128 * 4 + 2 * 4 * 4;   // the dw sums of two rows, and each epilogue
-                                                           // warp's wait status (double buffer)
-    static constexpr int SMEM = LT_BBYTES + NSLOT * LT_SLOT + XS + NB * 8 + 16 + 128;
+    static constexpr int NF = FR + 2;                     // frames per input slot
+    static constexpr int CHUNK_DATA = NF * RW * 16;       // one 8-channel chunk of NF frames
+    static constexpr int CHUNK = (CHUNK_DATA + 127) / 128 * 128;
+    static constexpr int SLOT = 4 * CHUNK;                // one input row: 4 chunks of 8 channels
+    static constexpr int CTAS = FR == 1 ? 2 : 1;          // CTAs per SM
+    static constexpr int COLS = 512 / CTAS;               // TMEM columns of the CTA
+    static constexpr int R = COLS / (16 * FR);            // blocks in one output frame's ring
+    static constexpr int NS = NSLOT;                      // input-row slots
+    static constexpr int NTHR = 32 * (2 + 4 * FR);        // producer, issuer, 4 epilogue warps per frame
+    // per frame: the dw sums of two rows and each epilogue warp's wait status (double buffer)
+    static constexpr int XS1 = 2 * 3 * 128 * 4 + 2 * 4 * 4;
+    static constexpr int XS = FR * XS1;
+    static constexpr int NB = 2 * NS + 2 * FR * R + 2;    // full, empty, accf[FR][R], acce[FR][R], wbar, drain
+    static constexpr int SMEM = LT_BBYTES + NS * SLOT + XS + NB * 8 + 16 + 128;
+    static_assert(R >= 4, "accumulator ring");
+    static_assert(FR <= 4, "named barriers 1..FR");
+    static_assert(SMEM * CTAS <= 227 * 1024, "shared memory");
 };
 
-__global__ void __launch_bounds__(NTHR, 1)
+template <int FR>
+__global__ void __launch_bounds__(LastCfg<FR>::NTHR, LastCfg<FR>::CTAS)
 conv_last_tc(const __grid_constant__ CUtensorMap xin, LastArgs a) {
+    using L = LastCfg<FR>;
     extern __shared__ __align__(128) unsigned char sm_raw[];
     unsigned char* sm = (unsigned char*)(((uintptr_t)sm_raw + 127) & ~(uintptr_t)127);
     unsigned char* wsm = sm;
     unsigned char* ring = sm + LT_BBYTES;
-    float* xs = reinterpret_cast<float*>(ring + NSLOT * LT_SLOT);   // [2][3][128]
-    uint64_t* bar = reinterpret_cast<uint64_t*>(ring + NSLOT * LT_SLOT + LastCfg::XS);
+    unsigned char* xs0 = ring + L::NS * L::SLOT;            // [FR][XS1]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(xs0 + L::XS);
     uint64_t* full = bar;
-    uint64_t* empty = bar + NSLOT;
-    uint64_t* accf = bar + 2 * NSLOT;            // [LT_R]: input row's D complete
-    uint64_t* acce = bar + 2 * NSLOT + LT_R;     // [LT_R]: block read by every output row that needs it
-    uint64_t* wbar = bar + 2 * NSLOT + 2 * LT_R;
+    uint64_t* empty = bar + L::NS;
+    uint64_t* accf = bar + 2 * L::NS;            // [FR][R]: input row's D complete
+    uint64_t* acce = accf + FR * L::R;           // [FR][R]: block read by every output row that needs it
+    uint64_t* wbar = acce + FR * L::R;
     uint64_t* drain = wbar + 1;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + LastCfg::NB);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + L::NB);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int HR = a.HR;
@@ -485,16 +501,17 @@ conv_last_tc(const __grid_constant__ CUtensorMap xin, LastArgs a) {
     const int hr = item % nhr;
     item /= nhr;
     const int ws = item % nws;
-    const int t = item / nws;
+    const int t0 = (item / nws) * FR;
+    const int nfr = min(FR, a.T - t0);           // output frames of this CTA
     const int w0 = ws * LT_W, hs = hr * HR, he = min(a.H, hs + HR);
     const int nout = he - hs, nin = nout + 2;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < NSLOT; ++i) {
+        for (int i = 0; i < L::NS; ++i) {
             mb_init(&full[i], 1);
             mb_init(&empty[i], 1);
         }
-        for (int i = 0; i < LT_R; ++i) {
+        for (int i = 0; i < FR * L::R; ++i) {
             mb_init(&accf[i], 1);
             mb_init(&acce[i], 4);
         }
@@ -504,7 +521,7 @@ conv_last_tc(const __grid_constant__ CUtensorMap xin, LastArgs a) {
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                     "r"(LT_COLS)
+                     "r"(L::COLS)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -519,41 +536,57 @@ conv_last_tc(const __grid_constant__ CUtensorMap xin, LastArgs a) {
             mb_expect(wbar, LT_BBYTES);
             bulk_g2s(wsm, a.wtap, LT_BBYTES, wbar);
             for (int i = 0; i < nin; ++i) {
-                const int s = i % NSLOT;
-                if (i >= NSLOT && !mb_wait(&empty[s], (uint32_t)((i / NSLOT - 1) & 1), a.flags)) break;
+                const int s = i % L::NS;
+                if (i >= L::NS && !mb_wait(&empty[s], (uint32_t)((i / L::NS - 1) & 1), a.flags)) break;
                 issued = i + 1;
-                mb_expect(&full[s], 4 * CHUNK_DATA);
-                unsigned char* dst = ring + s * LT_SLOT;
-                for (int k = 0; k < 4; ++k) tma4(dst + k * CHUNK_BYTES, &xin, &full[s], 8 * k, w0 - 1, hs - 1 + i, t - 1);
+                mb_expect(&full[s], 4 * L::CHUNK_DATA);
+                unsigned char* dst = ring + s * L::SLOT;
+                for (int k = 0; k < 4; ++k) tma4(dst + k * L::CHUNK, &xin, &full[s], 8 * k, w0 - 1, hs - 1 + i, t0 - 1);
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {   // ---------------- MMA issuer: six MMAs per input row into its block
+        if (lane == 0) {   // ---------------- MMA issuer: six MMAs per input row and output frame
             bool ok = mb_wait(wbar, 0, a.flags);
             const uint32_t wbase = su32(wsm), rbase = su32(ring);
             constexpr uint32_t ID = idesc_bf16(16);
             for (int i = 0; ok && i < nin; ++i) {
-                ok = mb_wait(&full[i % NSLOT], (uint32_t)((i / NSLOT) & 1), a.flags);
-                if (ok && i >= LT_R) ok = mb_wait(&acce[i % LT_R], (uint32_t)(((i - LT_R) / LT_R) & 1), a.flags);
+                ok = mb_wait(&full[i % L::NS], (uint32_t)((i / L::NS) & 1), a.flags);
+                // the blocks of row i: read back by every output row of row i - R
+                if (i >= L::R)
+                    for (int q = 0; ok && q < nfr; ++q)
+                        ok = mb_wait(&acce[q * L::R + i % L::R], (uint32_t)(((i - L::R) / L::R) & 1), a.flags);
                 if (!ok) break;
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)((i % LT_R) * 16);
-                const uint64_t a0 = sdesc(rbase + (uint32_t)((i % NSLOT) * LT_SLOT), CHUNK_BYTES, 128);
+                const uint64_t a0 = sdesc(rbase + (uint32_t)((i % L::NS) * L::SLOT), L::CHUNK, 128);
+                auto frame = [&](int q) {   // output frame t0 + q reads slot frames q, q + 1, q + 2
+                    const uint32_t d = tmem + (uint32_t)((q * L::R + i % L::R) * 16);
 #pragma unroll
-                for (int dt = 0; dt < 3; ++dt)
+                    for (int dt = 0; dt < 3; ++dt)
 #pragma unroll
-                    for (int ks = 0; ks < 2; ++ks) {
-                        const uint64_t ad = a0 + (uint64_t)((2 * ks * CHUNK_BYTES + dt * RW * 16) >> 4);
-                        const uint64_t bd = sdesc(wbase + (uint32_t)((dt * 2 + ks) * 512), 256, 128);
-                        umma(d, ad, bd, ID, (dt | ks) ? 1u : 0u);
-                    }
-                umma_commit(&empty[i % NSLOT]);
-                umma_commit(&accf[i % LT_R]);
+                        for (int ks = 0; ks < 2; ++ks) {
+                            const uint64_t ad = a0 + (uint64_t)((2 * ks * L::CHUNK + (q + dt) * RW * 16) >> 4);
+                            const uint64_t bd = sdesc(wbase + (uint32_t)((dt * 2 + ks) * 512), 256, 128);
+                            umma(d, ad, bd, ID, (dt | ks) ? 1u : 0u);
+                        }
+                };
+                if (nfr == FR) {   // all frames: one branch-free run of MMAs
+#pragma unroll
+                    for (int q = 0; q < FR; ++q) frame(q);
+                } else {
+                    for (int q = 0; q < nfr; ++q) frame(q);
+                }
+                umma_commit(&empty[i % L::NS]);
+                for (int q = 0; q < nfr; ++q) umma_commit(&accf[q * L::R + i % L::R]);
             }
         }
-    } else {   // ---------------- epilogue: warps 2..5
-        const int q = warp & 3;
-        const int l = q * 32 + lane;            // TMEM lane = voxel w0 - 1 + l
+    } else if (((warp - 2) >> 2) < nfr) {   // ---------------- epilogue: 4 warps per output frame
+        const int g = (warp - 2) >> 2;          // output frame t0 + g
+        const int qd = warp & 3;                // TMEM lane quadrant
+        const int l = qd * 32 + lane;           // TMEM lane = voxel w0 - 1 + l
+        const int t = t0 + g;
+        uint64_t* af = accf + g * L::R;
+        uint64_t* ae = acce + g * L::R;
+        float* xs = reinterpret_cast<float*>(xs0 + g * L::XS1);   // [2][3][128], then [2][4] statuses
         const float b = a.bias[0];
         for (int j = 0; j < nout; ++j) {
             float sdw[3] = {0.f, 0.f, 0.f};
@@ -561,10 +594,10 @@ conv_last_tc(const __grid_constant__ CUtensorMap xin, LastArgs a) {
 #pragma unroll
             for (int dh = 0; dh < 3; ++dh) {
                 const int r = j + dh;           // input row of offset dh
-                ok = ok && mb_wait(&accf[r % LT_R], (uint32_t)((r / LT_R) & 1), a.flags);
+                ok = ok && mb_wait(&af[r % L::R], (uint32_t)((r / L::R) & 1), a.flags);
                 tc_fence_after();
                 uint32_t v[16];
-                tmem_ld<16>(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)((r % LT_R) * 16), v);
+                tmem_ld<16>(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)((g * L::R + r % L::R) * 16), v);
                 tmem_ld_wait();
 #pragma unroll
                 for (int dw = 0; dw < 3; ++dw) sdw[dw] += __uint_as_float(v[3 * dh + dw]);
@@ -572,13 +605,13 @@ conv_last_tc(const __grid_constant__ CUtensorMap xin, LastArgs a) {
             // input row j is needed by no later output row
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mb_arrive(&acce[j % LT_R]);
+            if (lane == 0) mb_arrive(&ae[j % L::R]);
             float* xb = xs + (j & 1) * 3 * 128;
             int* okb = reinterpret_cast<int*>(xs + 2 * 3 * 128) + (j & 1) * 4;
 #pragma unroll
             for (int dw = 0; dw < 3; ++dw) xb[dw * 128 + l] = sdw[dw];
-            if (lane == 0) okb[q] = ok ? 1 : 0;
-            asm volatile("bar.sync 1, 128;" ::: "memory");
+            if (lane == 0) okb[qd] = ok ? 1 : 0;
+            asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
             // the four warps leave together if any of their waits gave up
             if (!(okb[0] & okb[1] & okb[2] & okb[3])) break;
             const int h = hs + j, w = w0 + l;
@@ -595,9 +628,9 @@ conv_last_tc(const __grid_constant__ CUtensorMap xin, LastArgs a) {
     if (*reinterpret_cast<volatile int*>(a.flags) & kFlagTimeout) {
         if (warp == 0 && lane == 0) {
             mb_settle(wbar, 0);
-            for (int s = 0; s < NSLOT && s < issued; ++s) {
-                const int last = s + ((issued - 1 - s) / NSLOT) * NSLOT;
-                mb_settle(&full[s], (uint32_t)((last / NSLOT) & 1));
+            for (int s = 0; s < L::NS && s < issued; ++s) {
+                const int last = s + ((issued - 1 - s) / L::NS) * L::NS;
+                mb_settle(&full[s], (uint32_t)((last / L::NS) & 1));
             }
         } else if (warp == 1 && lane == 0) {
             umma_commit(drain);
@@ -607,7 +640,7 @@ conv_last_tc(const __grid_constant__ CUtensorMap xin, LastArgs a) {
     }
     tc_fence_after();
     if (warp == 1)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(LT_COLS) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::COLS) : "memory");
 }
 
 // Taps of the last layer for conv_last_tc: out[((dt * 2 + ks) * 2 + chunk) * 16 + n][e] =
@@ -1099,29 +1132,45 @@ int run_conv(const void* in, int T, int H, int W, const __nv_bfloat16* wpack, co
                    : launch_conv<CIN, COUT, EPI, 1>(in, T, H, W, a, items, s);
 }
 
-// The last layer (32 -> 1) on its own kernel, 126-voxel tiles along w (conv_last_tc).
-int run_last(const __nv_bfloat16* in, int T, int H, int W, const __nv_bfloat16* wtap, const float* bias, float* z,
-             float* x0, int* flags, cudaStream_t s) {
+template <int FR>
+int launch_last(const __nv_bfloat16* in, int T, int H, int W, const LastArgs& a, int items, cudaStream_t s) {
+    using L = LastCfg<FR>;
     CUtensorMap m;
-    if (!act_map(&m, in, 32, T, H, W)) return nfail(SFSEG_ERR_CUDA, "tensor map encoding failed");
+    if (!act_map(&m, in, 32, T, H, W, L::NF)) return nfail(SFSEG_ERR_CUDA, "tensor map encoding failed");
     static bool attr = false;
     if (!attr) {
-        NET_CUDA(cudaFuncSetAttribute(conv_last_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, LastCfg::SMEM));
+        NET_CUDA(cudaFuncSetAttribute(conv_last_tc<FR>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM));
         attr = true;
     }
-    LastArgs a;
-    a.T = T; a.H = H; a.W = W;
-    a.wtap = wtap; a.bias = bias; a.z = z; a.x0 = x0; a.flags = flags;
-    int items = 0;
-    for (int hr : kHrChoices) {
-        a.HR = hr;
-        items = T * ((W + LT_W - 1) / LT_W) * ((H + hr - 1) / hr);
-        if (items >= 8 * num_sms()) break;   // two CTAs per SM, four waves
-    }
-    conv_last_tc<<<items, NTHR, LastCfg::SMEM, s>>>(m, a);
+    conv_last_tc<FR><<<items, L::NTHR, L::SMEM, s>>>(m, a);
     count_launches(1);
     NET_CUDA(cudaGetLastError());
     return SFSEG_OK;
+}
+
+// The last layer (32 -> 1) on its own kernel, 126-voxel tiles along w (conv_last_tc): four output
+// frames per CTA when that grid gives 4 waves (one CTA per SM) at some tile height, else one
+// (two CTAs per SM, 4 waves where the volume allows).
+int run_last(const __nv_bfloat16* in, int T, int H, int W, const __nv_bfloat16* wtap, const float* bias, float* z,
+             float* x0, int* flags, cudaStream_t s) {
+    LastArgs a;
+    a.T = T; a.H = H; a.W = W;
+    a.wtap = wtap; a.bias = bias; a.z = z; a.x0 = x0; a.flags = flags;
+    const int nws = (W + LT_W - 1) / LT_W;
+    for (int hr : kHrChoices) {
+        const int n = (T + 3) / 4 * nws * ((H + hr - 1) / hr);
+        if (n >= 4 * num_sms()) {
+            a.HR = hr;
+            return launch_last<4>(in, T, H, W, a, n, s);
+        }
+    }
+    int items = 0;
+    for (int hr : kHrChoices) {
+        a.HR = hr;
+        items = T * nws * ((H + hr - 1) / hr);
+        if (items >= 8 * num_sms()) break;
+    }
+    return launch_last<1>(in, T, H, W, a, items, s);
 }
 
 int pack_all(sfseg_net* n, cudaStream_t s) {

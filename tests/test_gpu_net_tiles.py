@@ -56,12 +56,14 @@ def _points(T, H, W, HR, seed, n_random=40):
     # 128-voxel tiles of the hidden layers, 126-voxel tiles of the last layer
     ws = {0, 1, 125, 126, 127, 128, 129, 251, 252, 255, 256, W - 129, W - 128, W - 2, W - 1}
     pts = set()
+    # frames 0..3 take every position inside a CTA's group of frames (two per CTA in the hidden
+    # layers, four in the last layer)
     for h in hs:
-        for t in (0, T // 2, T - 1):
+        for t in (0, 1, 2, 3, T // 2, T - 1):
             for w in (0, 125, 126, 127, 128, W - 1):
                 pts.add((t, h, w))
     for w in ws:
-        for t in (0, T - 1):
+        for t in (0, 1, 3, T - 1):
             for h in (0, HR - 1, HR, H - 1):
                 pts.add((t, h, w))
     rng = np.random.default_rng(seed)
@@ -124,32 +126,36 @@ def _input16(T, H, W, seed):
     return x
 
 
-def _last_layer_rows(T, H, W):
-    """The row count per CTA of the last layer's kernel (126-voxel tiles, two CTAs per SM)."""
+def _last_launch(T, H, W):
+    """(output frames, output rows) per CTA of the last layer's kernel (126-voxel tiles): four
+    frames when that grid gives 4 waves at one CTA per SM, else one frame, two CTAs per SM."""
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
     for hr in (64, 32, 16):
+        if -(-T // 4) * -(-W // 126) * -(-H // hr) >= 4 * nsm:
+            return 4, hr
+    for hr in (64, 32, 16):
         if T * -(-W // 126) * -(-H // hr) >= 8 * nsm:
-            return hr
-    return 16
+            return 1, hr
+    return 1, 16
 
 
-@pytest.mark.parametrize("shape,fr,hr,hr_last", [((17, 1024, 640), 2, 64, 64), ((8, 1024, 640), 2, 32, 32),
-                                                ((32, 256, 512), 2, 16, 32), ((2, 1024, 640), 1, 16, 16)],
+@pytest.mark.parametrize("shape,fr,hr,last", [((33, 1024, 640), 2, 64, (4, 64)), ((8, 1024, 640), 2, 32, (4, 16)),
+                                             ((32, 256, 512), 2, 16, (4, 16)), ((2, 1024, 640), 1, 16, (1, 16))],
                          ids=["rows64_odd_frames", "rows32", "rows16", "one_frame_per_cta"])
-def test_layers_at_production_tile_heights(sf, shape, fr, hr, hr_last):
+def test_layers_at_production_tile_heights(sf, shape, fr, hr, last):
     """Each layer's output at sampled voxels against the oracle's convolution of the GPU layer's
     own input, at the frames and tile height per CTA the launch picks for this volume (the last
-    layer's kernel picks its own, 64 rows as at 1080p for the first volume).  With 17 frames the
-    last CTA of each hidden layer computes one output frame instead of two; the 2-frame volume
-    runs one output frame per CTA."""
+    layer's kernel picks its own: four frames and 64 rows as at 1080p for the first volume).
+    With 33 frames the last CTA of each layer computes one output frame; the 2-frame volume runs
+    one output frame per CTA in both kernels."""
     T, H, W = shape
     assert _conv_launch(T, H, W) == (fr, hr)
-    assert _last_layer_rows(T, H, W) == hr_last
+    assert _last_launch(T, H, W) == last
     net = sf.WarmStartNet(C_IN, seed=11)
     params = _layer_params(net)
     x16 = _input16(T, H, W, 900 + hr)
     ins, z, x0 = _forward_layers(net, x16)
-    pts = _points(T, H, W, hr, seed=hr)
+    pts = sorted(set(_points(T, H, W, hr, seed=hr)) | set(_points(T, H, W, last[1], seed=hr + 1, n_random=0)))
     outs = [ins[1], ins[2], ins[3], z]
     for layer in range(4):
         _check_fwd(layer, ins[layer], outs[layer], params, pts, shape)
