@@ -588,28 +588,31 @@ conv_last_tc(const __grid_constant__ CUtensorMap xin, LastArgs a) {
         uint64_t* ae = acce + g * L::R;
         float* xs = reinterpret_cast<float*>(xs0 + g * L::XS1);   // [2][3][128], then [2][4] statuses
         const float b = a.bias[0];
-        for (int j = 0; j < nout; ++j) {
-            float sdw[3] = {0.f, 0.f, 0.f};
-            bool ok = true;
-#pragma unroll
-            for (int dh = 0; dh < 3; ++dh) {
-                const int r = j + dh;           // input row of offset dh
-                ok = ok && mb_wait(&af[r % L::R], (uint32_t)((r / L::R) & 1), a.flags);
-                tc_fence_after();
-                uint32_t v[16];
-                tmem_ld<16>(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)((g * L::R + r % L::R) * 16), v);
-                tmem_ld_wait();
-#pragma unroll
-                for (int dw = 0; dw < 3; ++dw) sdw[dw] += __uint_as_float(v[3 * dh + dw]);
-            }
-            // input row j is needed by no later output row
+        // Each input row's block is read once: its taps of offset dh go to the running sums of
+        // output row r - dh (pj[2]: row r - 2, complete after this row; pj[1]: r - 1; pj[0]: r).
+        float pj[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        bool ok = true;
+        for (int r = 0; r < nin; ++r) {
+            ok = ok && mb_wait(&af[r % L::R], (uint32_t)((r / L::R) & 1), a.flags);
+            tc_fence_after();
+            uint32_t v[16];
+            tmem_ld<16>(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)((g * L::R + r % L::R) * 16), v);
+            tmem_ld_wait();
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mb_arrive(&ae[j % L::R]);
+            if (lane == 0) mb_arrive(&ae[r % L::R]);   // the block is not read again
+#pragma unroll
+            for (int dw = 0; dw < 3; ++dw) {
+                pj[2][dw] = pj[1][dw] + __uint_as_float(v[6 + dw]);
+                pj[1][dw] = pj[0][dw] + __uint_as_float(v[3 + dw]);
+                pj[0][dw] = __uint_as_float(v[dw]);
+            }
+            const int j = r - 2;                 // output row completed by input row r
+            if (j < 0) continue;
             float* xb = xs + (j & 1) * 3 * 128;
             int* okb = reinterpret_cast<int*>(xs + 2 * 3 * 128) + (j & 1) * 4;
 #pragma unroll
-            for (int dw = 0; dw < 3; ++dw) xb[dw * 128 + l] = sdw[dw];
+            for (int dw = 0; dw < 3; ++dw) xb[dw * 128 + l] = pj[2][dw];
             if (lane == 0) okb[qd] = ok ? 1 : 0;
             asm volatile("bar.sync %0, 128;" ::"r"(1 + g) : "memory");
             // the four warps leave together if any of their waits gave up

@@ -46,6 +46,22 @@ def test_net_forward_matches_oracle(sf):
     net.close()
 
 
+@pytest.mark.parametrize("T", [1, 2])
+def test_net_forward_few_frames(sf, T):
+    """One and two frames: the convolution's two-frame CTAs (one output frame at T = 1) and the
+    last layer's frame groups with their zero-padded frames outside the volume."""
+    feats = _case(10 + T, T=T, H=20, W=40)
+    net = sf.WarmStartNet(8, seed=5)
+    p = net.get_params()
+    x0 = net.forward(torch.from_numpy(feats).cuda()).cpu().numpy().astype(np.float64)
+    params = [(_bf16(w), b.astype(np.float64)) for w, b in net.unflatten(p)]
+    ref, _ = oracle.warmstart_forward(_bf16(feats), params)
+    assert x0.shape == (T, 20, 40) and np.all(x0 > 0)
+    err = np.abs(x0 - ref).max() / np.abs(ref).max()
+    assert err < 3e-2, err
+    net.close()
+
+
 def test_net_gradients_match_oracle(sf):
     """Parameter gradients of the cosine loss (tensor-core data gradients + weight-gradient
     reduction) against the FP64 reverse pass of the plain loops."""
