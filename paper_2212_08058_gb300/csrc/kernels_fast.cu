@@ -566,11 +566,13 @@ static bool launch_t(const void* vin, void* out, const void* f, const Geom& g, c
     if (!make_map(&mv, vin, bf, g, C::BH) || !make_map(&mf, f, bf, g, C::BH)) return false;
     auto kern = iter_fast<RT, RH, RW, TS, TVO, OUT_X, SEP, MODE>;
     static int slots_per_sm = -1;
-    if (slots_per_sm < 0) {
+    static unsigned long long attr_set = 0;   // devices on which the attribute is set
+    if (!(attr_set & device_bit())) {
         if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM) != cudaSuccess) return false;
         int nb = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kern, NTHR, C::SMEM);
         slots_per_sm = nb > 0 ? nb : 1;
+        attr_set |= device_bit();
     }
     Params P;
     P.g = g;

@@ -166,6 +166,14 @@ void launch_soft_iou(const float* x, const float* tgt, int64_t n, float* grad, d
 
 int num_sms();
 
+// Bit of the current device in a per-call-site mask: kernel attributes (the dynamic shared-memory
+// size) are set per device, so a process that drives several GPUs sets them on each.
+inline unsigned long long device_bit() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    return 1ull << (dev & 63);
+}
+
 // Validates a neighbourhood (radius limits; sigma finite and > 0 where its radius is > 0) and
 // fills the three 1D Gaussian tap arrays exp(-d^2 / (2 sigma^2)), d = -r..r (all 1 at r = 0).
 // Returns SFSEG_OK, or INVALID_ARG / SHAPE with the thread's last-error message set (api.cu).

@@ -1096,10 +1096,10 @@ int launch_conv(const void* in, int T, int H, int W, const ConvArgs& a, int item
     CUtensorMap m;
     if (!act_map(&m, in, CIN, T, H, W, Cf::NF)) return nfail(SFSEG_ERR_CUDA, "tensor map encoding failed");
     auto k = conv3d_tc<CIN, COUT, EPI, FR>;
-    static bool attr = false;
-    if (!attr) {
+    static unsigned long long attr_set = 0;   // devices on which the attribute is set
+    if (!(attr_set & device_bit())) {
         NET_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM));
-        attr = true;
+        attr_set |= device_bit();
     }
     k<<<items, Cf::NTHR, Cf::SMEM, s>>>(m, a);
     count_launches(1);
@@ -1140,10 +1140,10 @@ int launch_last(const __nv_bfloat16* in, int T, int H, int W, const LastArgs& a,
     using L = LastCfg<FR>;
     CUtensorMap m;
     if (!act_map(&m, in, 32, T, H, W, L::NF)) return nfail(SFSEG_ERR_CUDA, "tensor map encoding failed");
-    static bool attr = false;
-    if (!attr) {
+    static unsigned long long attr_set = 0;   // devices on which the attribute is set
+    if (!(attr_set & device_bit())) {
         NET_CUDA(cudaFuncSetAttribute(conv_last_tc<FR>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::SMEM));
-        attr = true;
+        attr_set |= device_bit();
     }
     conv_last_tc<FR><<<items, L::NTHR, L::SMEM, s>>>(m, a);
     count_launches(1);
@@ -1247,10 +1247,10 @@ int run_wgrad(sfseg_net* n, int cout, int cin, const __nv_bfloat16* dz, const __
         return nfail(SFSEG_ERR_CUDA, "tensor map encoding failed");
     if (!n->wg_part) NET_CUDA(cudaMalloc(&n->wg_part, (size_t)num_sms() * WgCfg<4, 4>::PART * sizeof(float)));
     auto k = wgrad_tc<NCI, NCO>;
-    static bool attr = false;
-    if (!attr) {
+    static unsigned long long attr_set = 0;   // devices on which the attribute is set
+    if (!(attr_set & device_bit())) {
         NET_CUDA(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, Cf::SMEM));
-        attr = true;
+        attr_set |= device_bit();
     }
     WgArgs a;
     a.T = T; a.H = H; a.W = W;
