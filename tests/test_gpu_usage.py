@@ -1,4 +1,4 @@
-"""The calls the README shows, run as written on a small volume: every documented entry point
+"""The package's usage example, run as written on a small volume: every entry point it shows
 returns what its description says (shapes, unit norm, the residual, the autograd path, the online
 stream), and the first call agrees with the FP64 oracle."""
 import numpy as np
@@ -18,7 +18,7 @@ def sf():
     return sfseg
 
 
-def test_readme_use_section(sf):
+def test_usage_example(sf):
     C, T, H, W = 8, 8, 48, 96
     gen = torch.Generator(device="cuda").manual_seed(21)
     feats = torch.rand((C, T, H, W), device="cuda", generator=gen)      # soft masks / features in [0, 1]
