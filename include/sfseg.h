@@ -380,7 +380,8 @@ int sfseg_normalize(sfseg_handle* h, float* x, int64_t n, const double* acc_dev,
 int sfseg_check(sfseg_handle* h, void* stream);
 
 /* Which kernel ran the power-iteration steps (instrumentation; no counterpart in the paper).
- * The radii (1,3,3), (2,7,7), (1,4,4) and (1,2,2) run on the TMA-staged stencil kernel; other
+ * The radii (1,3,3), (2,7,7), (1,4,4), (1,2,2), (1,5,5), (2,3,3), (2,5,5) and (1,7,7) run on the
+ * TMA-staged stencil kernel; other
  * radii, or a volume whose tensor maps the driver does not encode, run on the generic streaming
  * stencil, which gives the same results more slowly.  Process-wide counts of steps issued on
  * each (host outputs; steps captured into a CUDA graph count once, at capture), and in

@@ -664,9 +664,10 @@ static bool dispatch_gpass(const float* vg, float* G, float* Qg, const float* Vk
 
 }  // namespace fast
 
-// Radii with a compiled kernel: the method's (1,3,3) and (2,7,7), and (1,4,4), (1,2,2), the
-// radii of (2,7,7) on 2x- and 4x-coarsened volumes (sfseg_coarse_start).
-#define SFSEG_FAST_RADII(X) X(1, 3, 3) X(2, 7, 7) X(1, 4, 4) X(1, 2, 2)
+// Radii with a compiled kernel: the method's (1,3,3) and (2,7,7); (1,4,4), (1,2,2), the radii of
+// (2,7,7) on 2x- and 4x-coarsened volumes (sfseg_coarse_start); and the neighbourhoods between
+// them, (1,5,5), (2,3,3), (2,5,5), (1,7,7).  Others run on the generic streaming stencil.
+#define SFSEG_FAST_RADII(X) X(1, 3, 3) X(2, 7, 7) X(1, 4, 4) X(1, 2, 2) X(1, 5, 5) X(2, 3, 3) X(2, 5, 5) X(1, 7, 7)
 
 bool fast_iterate_supported(const Taps& tp) {
 #define SFSEG_IS(A, B, C) if (tp.rt == A && tp.rh == B && tp.rw == C) return true;

@@ -36,12 +36,14 @@ def _gpu_grad(V, w, b, radius, K, every, grad_fn, p=0.1, alpha=1.0):
 
 
 @pytest.mark.parametrize("K,every,r", [(6, 2, (1, 2, 2)), (6, 4, (1, 2, 2)), (5, 5, (1, 2, 2)), (1, 3, (1, 2, 2)),
-                                        (6, 2, (1, 3, 3)), (5, 5, (2, 7, 7)), (3, 2, (1, 1, 2))])
+                                        (6, 2, (1, 3, 3)), (5, 5, (2, 7, 7)), (4, 2, (2, 3, 3)), (3, 3, (1, 5, 5)),
+                                        (3, 2, (1, 1, 2))])
 def test_adjoint_matches_oracle_gradient(K, every, r):
     """Linear loss <c, x_K>: the GPU adjoint equals the oracle's reverse pass on the explicit
     Eq. 2 matrix (4 x 12 x 12, C = 2), for several checkpoint spacings (K a multiple of the
-    spacing, not one, and below it); radii with a TMA kernel ((1,2,2), (1,3,3), (2,7,7): the
-    reverse pass in the stencil's state form) and without ((1,1,2): the six-signal stencil)."""
+    spacing, not one, and below it); radii with a TMA kernel ((1,2,2), (1,3,3), (2,7,7), (2,3,3),
+    (1,5,5): the reverse pass in the stencil's state form) and without ((1,1,2): the six-signal
+    stencil)."""
     V, _, _ = synth.multichannel(4, 12, 12, C=2, seed=4001)
     w = np.array([1.4, -0.7], dtype=np.float32)
     b = 0.1

@@ -1,5 +1,5 @@
 """A seeded sweep of small random problems against the FP64 oracle: volume shapes from one voxel
-up to several tiles with ragged edges, the four radii of the TMA kernel and others served by the
+up to several tiles with ragged edges, the eight radii of the TMA kernel and others served by the
 generic stencil, one or several channels (Eq. 9), float32 or bf16 features, a bf16 storage
 phase, uniform and S_m starts, per-axis Gaussian widths and alpha, p away from the defaults.
 Each case compares the unit-norm iterate (1e-5 with float32 storage, 2e-3 with a bf16 phase)
@@ -13,7 +13,7 @@ from paper_2212_08058_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-TMA_RADII = [(1, 3, 3), (2, 7, 7), (1, 4, 4), (1, 2, 2)]
+TMA_RADII = [(1, 3, 3), (2, 7, 7), (1, 4, 4), (1, 2, 2), (1, 5, 5), (2, 3, 3), (2, 5, 5), (1, 7, 7)]
 OTHER_RADII = [(0, 1, 1), (2, 2, 5), (3, 1, 0), (1, 8, 8), (4, 3, 2)]
 
 
@@ -30,7 +30,7 @@ def _case(i):
     T = int(rng.integers(1, 14))
     H = int(rng.choice([1, 2, 15, 16, 31, 47]))
     W = int(rng.choice([1, 7, 63, 64, 65, 130, 200]))
-    radius = TMA_RADII[i % 4] if i % 3 else OTHER_RADII[(i // 3) % len(OTHER_RADII)]
+    radius = TMA_RADII[i % len(TMA_RADII)] if i % 3 else OTHER_RADII[(i // 3) % len(OTHER_RADII)]
     C = int(rng.choice([1, 1, 3]))
     V = rng.uniform(0.0, 1.0, size=(C, T, H, W)).astype(np.float32)
     w = rng.normal(size=C).astype(np.float32) * 2.0 if C > 1 else None
