@@ -213,15 +213,23 @@ void launch_apply(const float* x, int x_pitch, float* y, int y_pitch, const floa
 }
 
 // v = u x from a caller-layout x into the internal layout (the state the iteration kernels read).
-__global__ void to_state_kernel(const float* x, const float* f32, const float* s32, float p, Geom g, float* v) {
-    for_each_voxel(g, [&](int64_t i, int64_t j) { v[j] = unary_pow_fast(s32 ? s32[j] : f32[j], p) * x[i]; });
+__global__ void to_state_kernel(const float* x, const float* f32, const float* s32, float p, Geom g, bool pairs,
+                                float* v) {
+    const float* sm = s32 ? s32 : f32;
+    for_each_voxel_pairs(
+        g, pairs,
+        [&](int64_t i, int64_t j) {
+            const float2 sv = ld2(sm + j), xv = ld2(x + i);
+            st2(v + j, make_float2(unary_pow_fast(sv.x, p) * xv.x, unary_pow_fast(sv.y, p) * xv.y));
+        },
+        [&](int64_t i, int64_t j) { v[j] = unary_pow_fast(sm[j], p) * x[i]; });
 }
 
 void launch_apply_user(const float* x, float* y, float* scratch_v, const float* f32, Geom g, const Taps& tp,
                        float inv_alpha, float p, int* flags, cudaStream_t s, const float* s32) {
     if (fast_iterate_supported(tp)) {
         const RowLaunch rl = row_launch(g, num_sms());
-        to_state_kernel<<<rl.blocks, rl.threads, 0, s>>>(x, f32, s32, p, g, scratch_v);
+        to_state_kernel<<<rl.blocks, rl.threads, 0, s>>>(x, f32, s32, p, g, g.W % 2 == 0 && aligned8(x), scratch_v);
         count_launches(1);
         // one unscaled step (no norm input) that writes x~ = A x into the caller's layout
         if (launch_iterate_fast(scratch_v, kF32, y, kF32, true, f32, g, tp, inv_alpha, p, nullptr, nullptr, flags, s,
@@ -234,50 +242,87 @@ void launch_apply_user(const float* x, float* y, float* scratch_v, const float* 
 // -------------------------------------------------------------------------- Eq. 9 combine
 template <typename TIn>
 __global__ void combine_kernel(const TIn* feat, int C, Geom g, const float* w, float bias, float* f32,
-                               __nv_bfloat16* fbf, int* flags) {
+                               __nv_bfloat16* fbf, int* flags, bool pairs) {
     const int64_t N = (int64_t)g.H * g.W * g.T;
     int bad = 0;
-    for_each_voxel(g, [&](int64_t i, int64_t j) {
-        float fv;
-        if (C == 1) {
-            fv = ldf(feat + i);
-        } else {
-            float z = bias;
-            for (int c = 0; c < C; ++c) z = fmaf(w[c], ldf(feat + (int64_t)c * N + i), z);
-            fv = 1.f / (1.f + expf(-z));
-        }
+    auto one = [&](int64_t i) {
+        if (C == 1) return ldf(feat + i);
+        float z = bias;
+        for (int c = 0; c < C; ++c) z = fmaf(w[c], ldf(feat + (int64_t)c * N + i), z);
+        return 1.f / (1.f + expf(-z));
+    };
+    auto check = [&](float fv) {
         if (!(fv >= 0.f) || isinf(fv)) bad = 1;
-        f32[j] = fv;
-        if (fbf) fbf[j] = __float2bfloat16_rn(fv);
-    });
+    };
+    for_each_voxel_pairs(
+        g, pairs,
+        [&](int64_t i, int64_t j) {
+            float2 fv;
+            if (C == 1) {
+                fv = ld2(feat + i);
+            } else {
+                float2 z = make_float2(bias, bias);
+                for (int c = 0; c < C; ++c) {
+                    const float2 x = ld2(feat + (int64_t)c * N + i);
+                    z.x = fmaf(w[c], x.x, z.x);
+                    z.y = fmaf(w[c], x.y, z.y);
+                }
+                fv = make_float2(1.f / (1.f + expf(-z.x)), 1.f / (1.f + expf(-z.y)));
+            }
+            check(fv.x);
+            check(fv.y);
+            st2(f32 + j, fv);
+            if (fbf) st2(fbf + j, fv);
+        },
+        [&](int64_t i, int64_t j) {
+            const float fv = one(i);
+            check(fv);
+            f32[j] = fv;
+            if (fbf) fbf[j] = __float2bfloat16_rn(fv);
+        });
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flags, kFlagBadFeature);
 }
 
 void launch_combine(const void* feat, int feat_dtype, int C, Geom g, const float* w_dev, float bias,
                     float* f32, __nv_bfloat16* fbf, int* flags, cudaStream_t s) {
     const RowLaunch rl = row_launch(g, num_sms());
+    // pairs of bf16 features need 4-byte alignment, of float32 8-byte, at every channel's start
+    const int64_t N = (int64_t)g.H * g.W * g.T;
+    const bool pairs = g.W % 2 == 0 && (feat_dtype == kF32 ? aligned8(feat) : ((uintptr_t)feat & 3) == 0) &&
+                       (C == 1 || N % 2 == 0);
     if (feat_dtype == kF32)
         combine_kernel<float><<<rl.blocks, rl.threads, 0, s>>>((const float*)feat, C, g, w_dev, bias, f32, fbf,
-                                                               flags);
+                                                               flags, pairs);
     else
         combine_kernel<__nv_bfloat16><<<rl.blocks, rl.threads, 0, s>>>((const __nv_bfloat16*)feat, C, g, w_dev,
-                                                                       bias, f32, fbf, flags);
+                                                                       bias, f32, fbf, flags, pairs);
     count_launches(1);
 }
 
 // ------------------------------------------------------------------------- start vector
 template <typename TV>
 __global__ void prologue_kernel(int init, const float* x_user, const float* f32, const float* s32, float p, Geom g,
-                                TV* v0, float* x_copy, float* x_user_out, double* acc0) {
+                                TV* v0, float* x_copy, float* x_user_out, double* acc0, bool pairs) {
     float part = 0.f;
-    for_each_voxel(g, [&](int64_t i, int64_t j) {
-        const float sv = s32 ? s32[j] : f32[j];
-        const float x = init == 0 ? x_user[i] : (init == 1 ? 1.f : sv);
-        part += x * x;
-        stf(v0 + j, unary_pow_fast(sv, p) * x);
-        if (x_copy) x_copy[j] = x;
-        if (x_user_out) x_user_out[i] = x;
-    });
+    const float* sm = s32 ? s32 : f32;
+    for_each_voxel_pairs(
+        g, pairs,
+        [&](int64_t i, int64_t j) {
+            const float2 sv = ld2(sm + j);
+            const float2 x = init == 0 ? ld2(x_user + i) : (init == 1 ? make_float2(1.f, 1.f) : sv);
+            part += x.x * x.x + x.y * x.y;
+            st2(v0 + j, make_float2(unary_pow_fast(sv.x, p) * x.x, unary_pow_fast(sv.y, p) * x.y));
+            if (x_copy) st2(x_copy + j, x);
+            if (x_user_out) st2(x_user_out + i, x);
+        },
+        [&](int64_t i, int64_t j) {
+            const float sv = sm[j];
+            const float x = init == 0 ? x_user[i] : (init == 1 ? 1.f : sv);
+            part += x * x;
+            stf(v0 + j, unary_pow_fast(sv, p) * x);
+            if (x_copy) x_copy[j] = x;
+            if (x_user_out) x_user_out[i] = x;
+        });
     const double b = block_sum((double)part);
     if (threadIdx.x == 0) atomicAdd(acc0, b);
 }
@@ -285,12 +330,14 @@ __global__ void prologue_kernel(int init, const float* x_user, const float* f32,
 void launch_prologue(int init, const float* x_user, const float* f32, float p, Geom g, void* v0, int vtype,
                      float* x_copy, float* x_user_out, double* acc0, cudaStream_t s, const float* s32) {
     const RowLaunch rl = row_launch(g, num_sms(), 8);
+    const bool pairs = g.W % 2 == 0 && aligned8(init == 0 ? x_user : nullptr, x_user_out);
     if (vtype == kF32)
         prologue_kernel<float><<<rl.blocks, rl.threads, 0, s>>>(init, x_user, f32, s32, p, g, (float*)v0, x_copy,
-                                                                x_user_out, acc0);
+                                                                x_user_out, acc0, pairs);
     else
         prologue_kernel<__nv_bfloat16><<<rl.blocks, rl.threads, 0, s>>>(init, x_user, f32, s32, p, g,
-                                                                        (__nv_bfloat16*)v0, x_copy, x_user_out, acc0);
+                                                                        (__nv_bfloat16*)v0, x_copy, x_user_out, acc0,
+                                                                        pairs);
     count_launches(1);
 }
 

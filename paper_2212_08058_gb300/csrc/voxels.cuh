@@ -18,6 +18,37 @@ __device__ __forceinline__ void for_each_voxel(const Geom& g, F&& f) {
     }
 }
 
+// With pairs: f2(i, j) for the column pairs (i, i + 1) of the caller layout and (j, j + 1) of the
+// internal layout, every row taken two columns at a time (W even, and every caller-layout array
+// 8-byte aligned, so that both layouts' pairs are 8-byte aligned: the pitch is a multiple of 32).
+// Without: f1(i, j) for every voxel, as for_each_voxel.
+template <typename F2, typename F1>
+__device__ __forceinline__ void for_each_voxel_pairs(const Geom& g, bool pairs, F2&& f2, F1&& f1) {
+    if (!pairs) {
+        for_each_voxel(g, f1);
+        return;
+    }
+    const int64_t rows = (int64_t)g.T * g.H;
+    const int np = g.W >> 1;
+    for (int64_t row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int64_t i0 = row * g.W, j0 = row * g.pitch;
+        for (int c = threadIdx.x; c < np; c += blockDim.x) f2(i0 + 2 * c, j0 + 2 * c);
+    }
+}
+
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+__device__ __forceinline__ float2 ld2(const __nv_bfloat16* p) {
+    return __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(p));
+}
+__device__ __forceinline__ void st2(float* p, float2 v) { *reinterpret_cast<float2*>(p) = v; }
+__device__ __forceinline__ void st2(__nv_bfloat16* p, float2 v) {
+    *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(v.x, v.y);
+}
+
+inline bool aligned8(const void* a, const void* b = nullptr, const void* c = nullptr) {
+    return (((uintptr_t)a | (uintptr_t)b | (uintptr_t)c) & 7) == 0;
+}
+
 // f4(i) for the groups [4i, 4i + 4) of [0, n) and f1(i) for the n % 4 elements after them when
 // vec (every array the caller touches is 16-byte aligned), else f1(i) for every element: the
 // flat element-wise passes then move 16 bytes per access.
