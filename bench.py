@@ -232,7 +232,7 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
-def bench_bf16_multichannel(sfseg, synth, steps: int = 10, with_parity: bool = True):
+def bench_bf16_multichannel(sfseg, synth, steps: int = 10):
     """SFSeg++ with bf16 storage: C = 8 bf16 channels of 64 x 480 x 854 (the multichannel recipe,
     drawn on the device), radius (2,7,7), 50 iterations all in bf16 storage.  Device-resident
     voxel-iterations/s, CUDA events."""
@@ -258,22 +258,89 @@ def bench_bf16_multichannel(sfseg, synth, steps: int = 10, with_parity: bool = T
            "value": nvox * ITERS * steps / (e0.elapsed_time(e1) * 1e-3), "unit": UNIT,
            "avg_launch_ms": it_ms / max(it_n, 1),
            "hbm_frac_of_measured": 6.0 * nvox / (it_ms * 1e-3 / max(it_n, 1)) / 1e9 / _peaks()[0]}
-    if with_parity:
-        # the error of this result: the same volume and schedule against the FP64 oracle on the
-        # bf16 channels widened exactly, at a bounded iteration count (the oracle takes about
-        # half a second per iteration of this volume on the host cores)
-        import numpy as np
-        import oracle
-        k = 10
-        xg = h.power_iterate(V, w, 0.0, RADIUS, iters=k, iters_bf16=k, x=x).cpu().numpy()
-        V64 = V.float().cpu().numpy().astype(np.float64)
-        f = oracle.combine(V64, w.astype(np.float64), 0.0)
-        del V64
-        xo, _ = oracle.power_filter(f, f, 0.1, 1.0, RADIUS, np.ones(f.shape), k)
-        out["parity"] = {"iterations": k, "vs": "FP64 oracle on the same bf16 channels, uniform start",
-                         **parity_stats(xg, xo, 2e-3)}
     h.close()
     return out
+
+
+# ---- the oracle leg's error statements (run with the cpu_baseline leg, after the GPU parts)
+
+def bf16_parity(sfseg, synth, k: int = 10):
+    """The error of the bf16 SFSeg++ result: the same volume and bf16 schedule against the FP64
+    oracle on the bf16 channels widened exactly, at a bounded iteration count (the oracle takes
+    about half a second per iteration of this volume on the host cores)."""
+    import numpy as np
+    import torch
+    import oracle
+    V, w = synth.multichannel_torch(T, H, W, 8, seed=3000, device="cuda", dtype=torch.bfloat16)
+    w = w.cpu().numpy()
+    with sfseg.PowerIteration(8, T, H, W) as h:
+        xg = h.power_iterate(V, w, 0.0, RADIUS, iters=k, iters_bf16=k).cpu().numpy()
+    V64 = V.float().cpu().numpy().astype(np.float64)
+    del V
+    f = oracle.combine(V64, w.astype(np.float64), 0.0)
+    del V64
+    xo, _ = oracle.power_filter(f, f, 0.1, 1.0, RADIUS, np.ones(f.shape), k)
+    return {"iterations": k, "vs": "FP64 oracle on the same bf16 channels, uniform start", **parity_stats(xg, xo, 2e-3)}
+
+
+def adjoint_parity(sfseg, synth, tol: float = 1e-3):
+    """The error of the differentiation result on the learning workload's check case (C = 2,
+    8 x 32 x 32, radius (1,3,3), 30 iterations, checkpoint every 5, 1 - soft-IoU): the adjoint's
+    dL/dw, dL/db against the FP64 oracle's reverse pass on the explicit Eq. 2 matrix, fed with
+    the oracle's own forward iterate and loss gradient."""
+    import numpy as np
+    import torch
+    import oracle
+    V, m, _ = synth.multichannel(8, 32, 32, C=2, seed=4002)
+    w, b, r, K = np.array([2.0, 1.0]), -1.0, (1, 3, 3), 30
+    tgt = (m > 0.5).astype(np.float64)
+    with sfseg.PowerIteration(2, 8, 32, 32) as h:
+        x = h.power_iterate(torch.from_numpy(V).cuda(), w.astype(np.float32), b, r, iters=K, record_every=5)
+        _, g = h.soft_iou_loss(x, torch.from_numpy(tgt.astype(np.float32)).cuda())
+        gw, gb = h.backward(g, r)
+    f = oracle.combine(V.astype(np.float64), w, b)
+    xo, _ = oracle.power_filter(f, f, 0.1, 1.0, r, np.ones(f.shape), K)
+    _, gK = oracle.soft_iou_loss(xo, tgt)
+    gwo, gbo = oracle.grad_csr(V.astype(np.float64), w, b, 0.1, 1.0, r, np.ones(f.size), K, gK)
+    got = np.append(np.asarray(gw, dtype=np.float64), float(gb))
+    ref = np.append(gwo, gbo)
+    err = float(np.abs(got - ref).max())
+    scale = float(np.abs(ref).max())
+    return {"case": "C=2 8x32x32, radius (1,3,3), 30 iterations, checkpoint every 5, 1 - soft-IoU",
+            "vs": "FP64 oracle reverse pass on the explicit Eq. 2 matrix (its own forward and loss gradient)",
+            "max_abs": err, "max_abs_over_max_grad": err / scale, "tolerance_rel": tol,
+            "within_tolerance": err <= tol * scale}
+
+
+def network_parity(sfseg, synth, tol: float = 3e-2):
+    """The error of the warm-start network's output (the trained weights, 8 bf16 channels and the
+    extra channel) on a small volume against the FP64 oracle's plain convolution loops on the
+    same bf16-rounded inputs and weights (three hidden activations are rounded to bf16 on the
+    GPU, hence the tolerance relative to max x0)."""
+    import numpy as np
+    import torch
+    import oracle
+    from paper_2212_08058_gb300 import warmstart
+    T_, H_, W_ = 3, 37, 140
+    gen = torch.Generator(device="cuda").manual_seed(7100)
+    feats = torch.rand((8, T_, H_, W_), device="cuda", generator=gen).to(torch.bfloat16)
+    extra = torch.rand((T_, H_, W_), device="cuda", generator=gen)
+    net = sfseg.WarmStartNet(9)
+    trained = warmstart.load(net)
+    params = [(synth.to_bf16_round(np.asarray(wt, dtype=np.float32)).astype(np.float64), bb.astype(np.float64))
+              for wt, bb in net.unflatten(net.get_params())]
+    x0 = net.forward(feats, extra).cpu().numpy().astype(np.float64)
+    net.check()
+    net.close()
+    inp = np.concatenate([feats.float().cpu().numpy().astype(np.float64),
+                          extra.to(torch.bfloat16).float().cpu().numpy().astype(np.float64)[None]], axis=0)
+    ref, _ = oracle.warmstart_forward(inp, params)
+    err = float(np.abs(x0 - ref).max())
+    scale = float(np.abs(ref).max())
+    return {"case": f"C=8+1 bf16 {T_}x{H_}x{W_}, {'trained' if trained else 'random-init'} weights",
+            "vs": "FP64 oracle convolution loops on the same bf16 inputs and weights",
+            "max_abs": err, "max_abs_over_max_x0": err / scale, "tolerance_rel": tol,
+            "within_tolerance": err <= tol * scale}
 
 
 def bench_soft_binarize(sfseg, synth, steps: int = 5, tail: int = 10):
@@ -850,6 +917,13 @@ def main():
             xg = h.power_iterate(feats, radius=RADIUS, iters=k, x=x).cpu().numpy()
             out["parity"] = {"iterations": k, "vs": "FP64 oracle (filter form), same volume, uniform start",
                              **parity_stats(xg, x_oracle, 1e-5)}
+            # the error of the other results, same leg
+            if "bf16_multichannel" in out:
+                out["bf16_multichannel"]["parity"] = bf16_parity(sfseg, synth)
+            if "adjoint" in out:
+                out["adjoint"]["parity"] = adjoint_parity(sfseg, synth)
+            if "net_training" in out:
+                out["net_training"]["parity"] = network_parity(sfseg, synth)
         print(json.dumps(out), flush=True)
     h.close()
     if world > 1:
