@@ -312,6 +312,80 @@ def adjoint_parity(sfseg, synth, tol: float = 1e-3):
             "within_tolerance": err <= tol * scale}
 
 
+def r133_parity(sfseg, synth, k: int = 10):
+    """The error of the radius (1,3,3) results (float32 and bf16 storage) on the 480p volume at a
+    bounded iteration count, against the FP64 oracle."""
+    import numpy as np
+    import torch
+    import oracle
+    Vn = synth.crossing_blobs(T, H, W, seed=SEED)
+    V = torch.from_numpy(Vn).cuda()
+    with sfseg.PowerIteration(1, T, H, W) as h:
+        x32 = h.power_iterate(V, radius=(1, 3, 3), iters=k).cpu().numpy()
+        x16 = h.power_iterate(V, radius=(1, 3, 3), iters=k, iters_bf16=k).cpu().numpy()
+    f = Vn[0].astype(np.float64)
+    xo, _ = oracle.power_filter(f, f, 0.1, 1.0, (1, 3, 3), np.ones(f.shape), k)
+    fb = synth.to_bf16_round(Vn[0]).astype(np.float64)
+    xb, _ = oracle.power_filter(fb, fb, 0.1, 1.0, (1, 3, 3), np.ones(f.shape), k)
+    return {"iterations": k, "vs": "FP64 oracle, same volume, uniform start (bf16: on the bf16-rounded features)",
+            "f32": parity_stats(x32, xo, 1e-5), "bf16": parity_stats(x16, xb, 2e-3)}
+
+
+def separate_maps_parity(sfseg, synth, k: int = 5):
+    """The error of the separate-map result (S_m and F_m from two draws) at a bounded iteration
+    count against the FP64 oracle with the same two maps."""
+    import numpy as np
+    import torch
+    import oracle
+    Vs, Vf = synth.crossing_blobs(T, H, W, seed=SEED), synth.crossing_blobs(T, H, W, seed=SEED + 1)
+    with sfseg.PowerIteration(1, T, H, W) as h:
+        h.set_features_sf(torch.from_numpy(Vs).cuda(), None, 0.0, torch.from_numpy(Vf).cuda())
+        xg = h.power_iterate(None, radius=RADIUS, iters=k).cpu().numpy()
+    xo, _ = oracle.power_filter(Vs[0].astype(np.float64), Vf[0].astype(np.float64), 0.1, 1.0, RADIUS,
+                                np.ones(Vs.shape[1:]), k)
+    return {"iterations": k, "vs": "FP64 oracle with the same S and F maps, uniform start", **parity_stats(xg, xo, 1e-5)}
+
+
+def soft_binarize_parity(sfseg, synth, k_cont: int = 5, k_tail: int = 2, gain: float = 10.0):
+    """The error of Alg. 1's soft-binarisation result on the 480p volume (a bounded run: k_cont
+    continuous iterations, then k_tail soft-binarisation steps) against the FP64 oracle's steps
+    from its own continuous iterate; and the share of voxels whose hard labels differ."""
+    import numpy as np
+    import torch
+    import oracle
+    Vn = synth.crossing_blobs(T, H, W, seed=SEED)
+    with sfseg.PowerIteration(1, T, H, W) as h:
+        xc = h.power_iterate(torch.from_numpy(Vn).cuda(), radius=RADIUS, iters=k_cont)
+        xs, mask = h.soft_binarize(xc, RADIUS, iters=k_tail, gain=gain)
+        xs, mask = xs.cpu().numpy().astype(np.float64), mask.cpu().numpy()
+    f = Vn[0].astype(np.float64)
+    xo, _ = oracle.power_filter(f, f, 0.1, 1.0, RADIUS, np.ones(f.shape), k_cont)
+    so, mo = oracle.soft_binarize(f, f, 0.1, 1.0, RADIUS, xo, k_tail, gain)
+    err = float(np.abs(xs - so).max())
+    return {"continuous_iterations": k_cont, "binarize_steps": k_tail, "gain": gain,
+            "vs": "FP64 oracle, same volume and steps", "max_abs": err, "tolerance_max_abs": 1e-5,
+            "within_tolerance": err <= 1e-5, "hard_label_mismatch_fraction": float((mask != mo).mean())}
+
+
+def online_parity(sfseg, synth, q: int = 13, iters: int = 10, frames: int = 3):
+    """The error of the online window after the first `frames` pushes of the 480p stream (window
+    q, iters per frame) against the FP64 oracle's Sec. 4.5 partial iterations."""
+    import numpy as np
+    import torch
+    import oracle
+    Vn = synth.crossing_blobs(T, H, W, seed=SEED)
+    V = torch.from_numpy(Vn).cuda()
+    with sfseg.OnlineStream(1, q, H, W) as st:
+        for k in range(frames):
+            st.push(V[:, k].contiguous(), radius=RADIUS, iters=iters)
+        win = st.window().cpu().numpy()
+    ref = oracle.online(Vn[:, :frames], None, 0.0, 0.1, 1.0, RADIUS, q, iters)[frames - 1]
+    err = float(np.abs(win - ref).max())
+    return {"frames": frames, "window": q, "iterations_per_frame": iters,
+            "vs": "FP64 oracle partial iterations (Sec. 4.5), same stream", "max_abs": err,
+            "tolerance_max_abs": 1e-5, "within_tolerance": err <= 1e-5}
+
+
 def network_parity(sfseg, synth, tol: float = 3e-2):
     """The error of the warm-start network's output (the trained weights, 8 bf16 channels and the
     extra channel) on a small volume against the FP64 oracle's plain convolution loops on the
@@ -924,6 +998,14 @@ def main():
                 out["adjoint"]["parity"] = adjoint_parity(sfseg, synth)
             if "net_training" in out:
                 out["net_training"]["parity"] = network_parity(sfseg, synth)
+            if "r133_storage" in out:
+                out["r133_storage"]["parity"] = r133_parity(sfseg, synth)
+            if "separate_maps" in out:
+                out["separate_maps"]["parity"] = separate_maps_parity(sfseg, synth)
+            if "soft_binarize" in out:
+                out["soft_binarize"]["parity"] = soft_binarize_parity(sfseg, synth)
+            if "online" in out:
+                out["online"]["parity"] = online_parity(sfseg, synth)
         print(json.dumps(out), flush=True)
     h.close()
     if world > 1:
