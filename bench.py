@@ -386,6 +386,26 @@ def online_parity(sfseg, synth, q: int = 13, iters: int = 10, frames: int = 3):
             "tolerance_max_abs": 1e-5, "within_tolerance": err <= 1e-5}
 
 
+def small_graphs_parity(sfseg, synth):
+    """The error of the small case's result as the bench runs it, replayed from a CUDA graph (the
+    first call captures, the next ones replay), against the FP64 oracle: 8 x 64 x 64 drifting
+    blob, radius (1,3,3), 20 iterations from the uniform start."""
+    import numpy as np
+    import torch
+    import oracle
+    Vn = synth.drifting_blob(8, 64, 64, seed=1000)
+    with sfseg.PowerIteration(1, 8, 64, 64) as h:
+        h.set_features(torch.from_numpy(Vn).cuda())
+        h.enable_graphs(True)
+        x = torch.empty((8, 64, 64), device="cuda")
+        for _ in range(3):
+            h.power_iterate(None, radius=(1, 3, 3), iters=20, x=x)
+        xg = x.cpu().numpy()
+    f = Vn[0].astype(np.float64)
+    xo, _ = oracle.power_filter(f, f, 0.1, 1.0, (1, 3, 3), np.ones(f.shape), 20)
+    return {"iterations": 20, "vs": "FP64 oracle, uniform start (graph replay)", **parity_stats(xg, xo, 1e-5)}
+
+
 def network_parity(sfseg, synth, tol: float = 3e-2):
     """The error of the warm-start network's output (the trained weights, 8 bf16 channels and the
     extra channel) on a small volume against the FP64 oracle's plain convolution loops on the
@@ -1006,6 +1026,8 @@ def main():
                 out["soft_binarize"]["parity"] = soft_binarize_parity(sfseg, synth)
             if "online" in out:
                 out["online"]["parity"] = online_parity(sfseg, synth)
+            if "small_graphs" in out:
+                out["small_graphs"]["parity"] = small_graphs_parity(sfseg, synth)
         print(json.dumps(out), flush=True)
     h.close()
     if world > 1:
