@@ -406,6 +406,26 @@ def small_graphs_parity(sfseg, synth):
     return {"iterations": 20, "vs": "FP64 oracle, uniform start (graph replay)", **parity_stats(xg, xo, 1e-5)}
 
 
+def exact_parity(sfseg, synth, K: int = 15):
+    """The error of the exact (Eq. 1) operator's power iteration at the study's radius (2,7,7), on
+    a volume small enough for the oracle's explicit Eq. 1 matrix (4 x 20 x 40 drifting blob),
+    K normalised steps from the uniform start."""
+    import numpy as np
+    import torch
+    import oracle
+    T_, H_, W_, r = 4, 20, 40, (2, 7, 7)
+    Vn = synth.drifting_blob(T_, H_, W_, seed=7601)
+    f = Vn[0].astype(np.float64)
+    Me = oracle.affinity(f, f, 0.1, 1.0, r, exact=True)
+    xo, _ = oracle.power_csr(Me, np.ones(T_ * H_ * W_), K)
+    with sfseg.PowerIteration(1, T_, H_, W_) as h:
+        h.set_features(torch.from_numpy(Vn).cuda())
+        xg = h.power_iterate_exact(r, iters=K).cpu().numpy()
+    return {"case": f"drifting blob {T_}x{H_}x{W_}, radius (2,7,7), {K} steps",
+            "vs": "FP64 oracle power iteration on the explicit Eq. 1 matrix",
+            **parity_stats(xg, xo.reshape(T_, H_, W_), 1e-5)}
+
+
 def network_parity(sfseg, synth, tol: float = 3e-2):
     """The error of the warm-start network's output (the trained weights, 8 bf16 channels and the
     extra channel) on a small volume against the FP64 oracle's plain convolution loops on the
@@ -1028,6 +1048,8 @@ def main():
                 out["online"]["parity"] = online_parity(sfseg, synth)
             if "small_graphs" in out:
                 out["small_graphs"]["parity"] = small_graphs_parity(sfseg, synth)
+            if "exact_kernel" in out:
+                out["exact_kernel"]["parity"] = exact_parity(sfseg, synth)
         print(json.dumps(out), flush=True)
     h.close()
     if world > 1:
