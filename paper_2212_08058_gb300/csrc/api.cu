@@ -1024,12 +1024,21 @@ int sfseg_soft_binarize(sfseg_handle* h, const sfseg_neighborhood* nb, int iters
     const float* s32 = h->sep ? h->s32 : nullptr;
     for (int k = 0; k < iters; ++k) {
         const bool last = k == iters - 1;
-        if (k == 0 || !fast)
-            launch_apply_user(x_inout, y, v, h->f32, h->g, tp, inv_alpha, p, h->flags, s, s32);
-        else if (!launch_iterate_fast(v, kF32, y, kF32, true, h->f32, h->g, tp, inv_alpha, p, nullptr, nullptr,
-                                      h->flags, s, s32))
-            return fail(SFSEG_ERR_CUDA, "stencil launch failed");
-        launch_max_key(y, h->N, key, s);
+        bool fused = false;   // the stencil took max(y) itself (shared maps, a compiled radius)
+        if (fast && !s32) {
+            SFSEG_CUDA(cudaMemsetAsync(key, 0, sizeof(unsigned), s));
+            if (k == 0) launch_to_state(x_inout, h->f32, nullptr, p, h->g, v, s);
+            fused = launch_iterate_fast_max(v, y, h->f32, h->g, tp, inv_alpha, p, key, h->flags, s);
+            if (!fused && k > 0) return fail(SFSEG_ERR_CUDA, "stencil launch failed");
+        }
+        if (!fused) {
+            if (k == 0 || !fast)
+                launch_apply_user(x_inout, y, v, h->f32, h->g, tp, inv_alpha, p, h->flags, s, s32);
+            else if (!launch_iterate_fast(v, kF32, y, kF32, true, h->f32, h->g, tp, inv_alpha, p, nullptr, nullptr,
+                                          h->flags, s, s32))
+                return fail(SFSEG_ERR_CUDA, "stencil launch failed");
+            launch_max_key(y, h->N, key, s);
+        }
         launch_sigmoid_step(y, key, gain, center, h->f32, p, h->g, x_inout, (fast && !last) ? v : nullptr,
                             last ? mask_out : nullptr, h->flags, s, s32);
         SFSEG_LAUNCHED();

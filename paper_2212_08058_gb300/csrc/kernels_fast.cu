@@ -30,6 +30,7 @@
 
 #include "common.cuh"
 #include "launch.h"
+#include "order_key.cuh"
 
 namespace sfseg {
 namespace fast {
@@ -159,6 +160,7 @@ struct Params {
     int exj, exlast;
     float exc[3];     // c_{3j}, c_{3j+1}, c_{3j+2}
     float ex_alpha;
+    unsigned* maxkey; // MODE 8: atomicMax of the order key of the largest output
 };
 
 // SEP: the unary term u = s^p comes from a separate map S_m (Eq. 9 with its own channels)
@@ -176,7 +178,9 @@ struct Params {
 // terms n = 3j (G*v), 3j + 1 (G*(f v)) and 3j + 2 (G*(f^2 v)); it adds
 // t = f^{3j} (c_{3j} G*v + f (c_{3j+1} G*(f v) + f c_{3j+2} G*(f^2 v))) to out (writes it when
 // j = 0), and on the last term stores y = u e^{-a f^2} / a * (sum of the terms) and adds |y|^2 to
-// acc_out.  All in the internal layout.
+// acc_out.  All in the internal layout.  MODE 8 is the step (MODE 0) that also takes the
+// largest of its outputs and adds it to P.maxkey (atomicMax of the order key, one per CTA): the
+// maximum a soft-binarisation step (Alg. 1 step 3) scales by, without a pass of its own.
 template <int RT, int RH, int RW, typename TS, typename TVO, bool OUT_X, bool SEP, int MODE>
 __global__ void __launch_bounds__(NTHR, SFSEG_FAST_MINB)
 iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtensorMap mf, Params P) {
@@ -250,6 +254,7 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
 #pragma unroll
             for (int m = 0; m < 4; ++m) st[a][k][m] = make_float2(0.f, 0.f);
     float2 part = make_float2(0.f, 0.f);
+    float tmax = 0.f;   // MODE 8: the largest output so far (outputs are >= 0)
     bool ok = true;
 
     if (tid == 0)
@@ -383,11 +388,12 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
                     for (int i = 0; i < P.exj; ++i) F = mul2(F, f3);
                     const float2 inner = fma2(mul2(fv, f2(P.exc[2])), y[1][m], mul2(f2(P.exc[1]), y[2][m]));
                     outv[m] = mul2(F, fma2(fv, inner, mul2(f2(P.exc[0]), y[0][m])));
-                } else if constexpr (MODE == 0 || MODE == 4 || MODE == 6) {
+                } else if constexpr (MODE == 0 || MODE == 4 || MODE == 6 || MODE == 8) {
                     float2 B = fma2(e, y[0][m], make_float2(-y[1][m].x, -y[1][m].y));
                     B = fma2(mul2(f2(2.f), fv), y[2][m], B);
                     const float2 xt = mul2(mul2(s2, u), B);
                     part = fma2(xt, xt, part);
+                    if constexpr (MODE == 8) tmax = fmaxf(tmax, fmaxf(xt.x, xt.y));
                     outv[m] = OUT_X ? xt : mul2(u, xt);
                     if constexpr (MODE == 4) outq[m] = xt;
                     if constexpr (MODE == 6) {
@@ -503,6 +509,17 @@ iter_fast(const __grid_constant__ CUtensorMap mv, const __grid_constant__ CUtens
     }
     const double tot = block_sum((double)part.x + (double)part.y);
     if (tid == 0 && P.acc_out) atomicAdd(P.acc_out, tot);
+    if constexpr (MODE == 8) {
+        __shared__ unsigned wmax[NTHR / 32];
+        const unsigned kmax = __reduce_max_sync(0xffffffffu, order_key(tmax));
+        if (lane == 0) wmax[warp] = kmax;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned m = wmax[0];
+            for (int i = 1; i < NTHR / 32; ++i) m = max(m, wmax[i]);
+            atomicMax(P.maxkey, m);
+        }
+    }
 }
 
 // ------------------------------------------------------------------------------- host side
@@ -559,7 +576,8 @@ static int pick_chunk(int T, int tiles, int slots, int rt) {
 template <int RT, int RH, int RW, typename TS, typename TVO, bool OUT_X, bool SEP = false, int MODE = 0>
 static bool launch_t(const void* vin, void* out, const void* f, const Geom& g, const Taps& tp, float inv_alpha,
                      float p, const double* acc_in, double* acc_out, int* flags, cudaStream_t s,
-                     const float* s32 = nullptr, void* out2 = nullptr, const ExactTerm* ex = nullptr) {
+                     const float* s32 = nullptr, void* out2 = nullptr, const ExactTerm* ex = nullptr,
+                     unsigned* maxkey = nullptr) {
     using C = Cfg<RT, RH, RW, TS, TVO, OUT_X>;
     constexpr bool bf = sizeof(TS) == 2;
     CUtensorMap mv, mf;
@@ -588,6 +606,7 @@ static bool launch_t(const void* vin, void* out, const void* f, const Geom& g, c
     P.exlast = ex ? ex->last : 0;
     for (int i = 0; i < 3; ++i) P.exc[i] = ex ? ex->c[i] : 0.f;
     P.ex_alpha = ex ? ex->alpha : 0.f;
+    P.maxkey = maxkey;
     const int tx = (g.W + TW - 1) / TW, ty = (g.H + TH - 1) / TH;
     P.tchunk = pick_chunk(g.T, tx * ty, slots_per_sm * num_sms(), RT);
     P.acc_in = acc_in;
@@ -655,6 +674,15 @@ static bool dispatch_exact(const float* v, float* y, const float* f, const Geom&
                                                              nullptr, &ex);
 }
 
+// The step into the caller layout that also adds its largest output to *maxkey (MODE 8),
+// float32, shared maps.
+template <int RT, int RH, int RW>
+static bool dispatch_max(const float* vin, float* y, const float* f, const Geom& g, const Taps& tp, float ia, float p,
+                         unsigned* maxkey, int* fl, cudaStream_t s) {
+    return launch_t<RT, RH, RW, float, float, true, false, 8>(vin, y, f, g, tp, ia, p, nullptr, nullptr, fl, s, nullptr,
+                                                            nullptr, nullptr, maxkey);
+}
+
 // The adjoint's g-pass in state form (MODE 5), float32 only.
 template <int RT, int RH, int RW>
 static bool dispatch_gpass(const float* vg, float* G, float* Qg, const float* Vk, const float* f, const Geom& g,
@@ -683,6 +711,16 @@ bool launch_iterate_fast(const void* vin, int vin_type, void* out, int out_type,
     if (tp.rt == A && tp.rh == B && tp.rw == C)                                                             \
         return fast::dispatch<A, B, C>(vin, vin_type, out, out_type, out_x, f, g, tp, inv_alpha, p, acc_in, \
                                        acc_out, flags, s, s32);
+    SFSEG_FAST_RADII(SFSEG_GO)
+#undef SFSEG_GO
+    return false;
+}
+
+bool launch_iterate_fast_max(const float* vin, float* y, const float* f, const Geom& g, const Taps& tp,
+                             float inv_alpha, float p, unsigned* maxkey, int* flags, cudaStream_t s) {
+#define SFSEG_GO(A, B, C)                                                                                 \
+    if (tp.rt == A && tp.rh == B && tp.rw == C)                                                           \
+        return fast::dispatch_max<A, B, C>(vin, y, f, g, tp, inv_alpha, p, maxkey, flags, s);
     SFSEG_FAST_RADII(SFSEG_GO)
 #undef SFSEG_GO
     return false;

@@ -225,6 +225,12 @@ __global__ void to_state_kernel(const float* x, const float* f32, const float* s
         [&](int64_t i, int64_t j) { v[j] = unary_pow_fast(sm[j], p) * x[i]; });
 }
 
+void launch_to_state(const float* x, const float* f32, const float* s32, float p, Geom g, float* v, cudaStream_t s) {
+    const RowLaunch rl = row_launch(g, num_sms());
+    to_state_kernel<<<rl.blocks, rl.threads, 0, s>>>(x, f32, s32, p, g, g.W % 2 == 0 && aligned8(x), v);
+    count_launches(1);
+}
+
 void launch_apply_user(const float* x, float* y, float* scratch_v, const float* f32, Geom g, const Taps& tp,
                        float inv_alpha, float p, int* flags, cudaStream_t s, const float* s32) {
     if (fast_iterate_supported(tp)) {

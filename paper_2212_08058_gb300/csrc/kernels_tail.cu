@@ -6,7 +6,8 @@
 // so that gain and centre mean the same thing for any volume size (the paper leaves the
 // sigmoid's parameterisation open).
 //
-// A step is the stencil launch (y in caller layout), one reduction for max(y), and one
+// A step is the stencil launch (y in caller layout; for shared maps and a radius with a TMA
+// kernel the launch also takes max(y), kernels_fast.cu mode 8, else one reduction does), and one
 // elementwise pass that writes x, and, for the next step, the stencil's input state u * x in
 // the internal layout (so the next stencil launch needs no separate conversion).
 #include "common.cuh"

@@ -36,13 +36,23 @@ void launch_iterate(const void* vin, int vin_type, void* out, int out_type, bool
                     float inv_alpha, float p, const double* acc_in, double* acc_out, int* flags,
                     cudaStream_t s, const float* s32 = nullptr);
 
-// TMA-staged step for the radii (1,3,3), (2,7,7), (1,4,4) and (1,2,2) (kernels_fast.cu).  s32
+// TMA-staged step for the radii with a compiled kernel (kernels_fast.cu).  s32
 // (nullable): a separate unary map (float32 storage only).  Returns false when the radius has no
 // compiled kernel or a tensor map cannot be encoded; nothing is launched then.
 bool fast_iterate_supported(const Taps& tp);
 bool launch_iterate_fast(const void* vin, int vin_type, void* out, int out_type, bool out_x, const void* f,
                          const Geom& g, const Taps& tp, float inv_alpha, float p, const double* acc_in,
                          double* acc_out, int* flags, cudaStream_t s, const float* s32 = nullptr);
+
+// The TMA step from the state vin (internal layout, float32) to y = A x in the caller layout that
+// also adds the order key of its largest output to *maxkey (atomicMax; zero it first): a
+// soft-binarisation step's maximum without a pass of its own.  No norm scaling.  False (nothing
+// launched) for a radius without a compiled kernel.
+bool launch_iterate_fast_max(const float* vin, float* y, const float* f, const Geom& g, const Taps& tp,
+                             float inv_alpha, float p, unsigned* maxkey, int* flags, cudaStream_t s);
+
+// v = u x (internal layout) for a caller-layout x, u = s^p with s the unary map (s32, or f32).
+void launch_to_state(const float* x, const float* f32, const float* s32, float p, Geom g, float* v, cudaStream_t s);
 
 // The TMA step that also records x~_{k+1} (internal layout) into ckpt, float32 storage; false
 // (nothing launched) for a radius without a compiled kernel.
