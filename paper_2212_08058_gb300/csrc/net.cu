@@ -685,7 +685,10 @@ constexpr int WG_XV = MT + 2;                              // x voxels per row (
 constexpr int WG_CHA = (WG_XV * 16 + 127) / 128 * 128;     // A chunk stride (2176 B)
 constexpr int WG_CHB = MT * 16;                            // B chunk stride (2048 B)
 constexpr int WG_A_BYTES = 16 * WG_CHA;                    // 4 row blocks x 4 chunks
-constexpr int WG_NS = 3;                                   // stages
+#ifndef SFSEG_NET_WG_NS
+#define SFSEG_NET_WG_NS 3
+#endif
+constexpr int WG_NS = SFSEG_NET_WG_NS;   // stages (2 measured 4 % slower; 4 do not fit beside the partial sums)
 
 template <int NCI, int NCO>
 struct WgCfg {
