@@ -688,7 +688,7 @@ constexpr int WG_A_BYTES = 16 * WG_CHA;                    // 4 row blocks x 4 c
 #ifndef SFSEG_NET_WG_NS
 #define SFSEG_NET_WG_NS 3
 #endif
-constexpr int WG_NS = SFSEG_NET_WG_NS;   // stages (2 measured 4 % slower; 4 do not fit beside the partial sums)
+constexpr int WG_NS = SFSEG_NET_WG_NS;   // stages (2 measured 4 % slower; 4 exceed the shared memory)
 
 template <int NCI, int NCO>
 struct WgCfg {
