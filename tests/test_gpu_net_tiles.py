@@ -37,9 +37,10 @@ def sf():
 
 def _conv_launch(T, H, W):
     """(output frames, output rows) per CTA that the convolution launch picks for this volume
-    (see net.cu): two frames when that grid still gives 4 waves at some tile height, else one."""
+    (see net.cu): three frames when that grid still gives 4 waves at some tile height, else two,
+    else one."""
     nsm = torch.cuda.get_device_properties(0).multi_processor_count
-    for fr in (2, 1):
+    for fr in (3, 2, 1):
         for hr in (64, 32, 16):
             if -(-T // fr) * -(-W // 128) * -(-H // hr) >= 4 * nsm:
                 return fr, hr
@@ -139,15 +140,17 @@ def _last_launch(T, H, W):
     return 1, 16
 
 
-@pytest.mark.parametrize("shape,fr,hr,last", [((33, 1024, 640), 2, 64, (4, 64)), ((8, 1024, 640), 2, 32, (4, 16)),
-                                             ((32, 256, 512), 2, 16, (4, 16)), ((2, 1024, 640), 1, 16, (1, 16))],
-                         ids=["rows64_odd_frames", "rows32", "rows16", "one_frame_per_cta"])
+@pytest.mark.parametrize("shape,fr,hr,last", [((35, 1024, 640), 3, 64, (4, 64)), ((17, 1024, 640), 3, 32, (4, 32)),
+                                             ((32, 256, 512), 3, 16, (4, 16)), ((5, 1024, 512), 2, 16, (4, 16)),
+                                             ((2, 1024, 640), 1, 16, (1, 16))],
+                         ids=["rows64_partial_groups", "rows32", "rows16", "two_frames_per_cta", "one_frame_per_cta"])
 def test_layers_at_production_tile_heights(sf, shape, fr, hr, last):
     """Each layer's output at sampled voxels against the oracle's convolution of the GPU layer's
     own input, at the frames and tile height per CTA the launch picks for this volume (the last
     layer's kernel picks its own: four frames and 64 rows as at 1080p for the first volume).
-    With 33 frames the last CTA of each layer computes one output frame; the 2-frame volume runs
-    one output frame per CTA in both kernels."""
+    Frame counts that the groups do not divide leave the last CTA of a layer with fewer output
+    frames (35 = 11 x 3 + 2 and 8 x 4 + 3; 17 = 5 x 3 + 2; 5 = 2 x 2 + 1); the 2-frame volume
+    runs one output frame per CTA in both kernels."""
     T, H, W = shape
     assert _conv_launch(T, H, W) == (fr, hr)
     assert _last_launch(T, H, W) == last
@@ -166,12 +169,13 @@ def test_layers_at_production_tile_heights(sf, shape, fr, hr, last):
     net.close()
 
 
-@pytest.mark.parametrize("shape,hr", [((17, 1024, 640), 64), ((8, 1024, 640), 32)], ids=["rows64_odd_frames", "rows32"])
-def test_data_gradient_at_production_tile_heights(sf, shape, hr):
+@pytest.mark.parametrize("shape,fr,hr", [((35, 1024, 640), 3, 64), ((17, 1024, 640), 3, 32), ((5, 1024, 512), 2, 16)],
+                         ids=["rows64_partial_groups", "rows32", "two_frames_per_cta"])
+def test_data_gradient_at_production_tile_heights(sf, shape, fr, hr):
     """dx = conv^T(dz) * [x > 0] of layers 1..3 (the data-gradient convolution on the tensor
     cores) at sampled voxels against the oracle's reverse loops on the same bf16 inputs."""
     T, H, W = shape
-    assert _conv_launch(T, H, W) == (2, hr)
+    assert _conv_launch(T, H, W) == (fr, hr)
     net = sf.WarmStartNet(C_IN, seed=12)
     params = _layer_params(net)
     ins, _, _ = _forward_layers(net, _input16(T, H, W, 910 + hr))
@@ -256,13 +260,14 @@ def test_weight_gradient_training_volume(sf):
     net.close()
 
 
-@pytest.mark.parametrize("shape,hr", [((17, 1024, 640), 64), ((8, 1024, 640), 32)], ids=["rows64_odd_frames", "rows32"])
-def test_network_sampled_at_production_tile_heights(sf, shape, hr):
+@pytest.mark.parametrize("shape,fr,hr", [((35, 1024, 640), 3, 64), ((17, 1024, 640), 3, 32)],
+                         ids=["rows64_partial_groups", "rows32"])
+def test_network_sampled_at_production_tile_heights(sf, shape, fr, hr):
     """sfseg_net_forward (8 bf16 channels + the extra channel) at sampled voxels against the
     oracle's FP64 network on the 9 x 9 x 9 crop around each voxel, within the end-to-end bf16
     tolerance of the small network test (three hidden activations rounded to bf16)."""
     T, H, W = shape
-    assert _conv_launch(T, H, W) == (2, hr)
+    assert _conv_launch(T, H, W) == (fr, hr)
     gen = torch.Generator(device="cuda").manual_seed(940 + hr)
     feats = torch.rand((8, T, H, W), device="cuda", generator=gen).to(torch.bfloat16)
     extra = torch.rand((T, H, W), device="cuda", generator=gen)
