@@ -317,6 +317,14 @@ int sfseg_net_layer_backward(sfseg_net* net, int layer, const void* in, const vo
  * kernels gave up since the last check (then clears the flag), else OK. */
 int sfseg_net_check(sfseg_net* net, void* stream);
 
+/* Launch shape of the network's convolutions (instrumentation; no counterpart in the paper).
+ * For kernel 0 (the hidden-layer kernel: the forward of layers 0..2 and the data gradients of
+ * layers 1..3) or 1 (the last layer's forward), the shape of the calling thread's most recent
+ * launch of it: output frames per CTA (3, 2 or 1; 4 or 1 for kernel 1), output rows per CTA
+ * (64, 32 or 16) and the number of CTAs; all three 0 before the first launch.  Host outputs.
+ * Errors: INVALID_ARG (kernel not 0 or 1, null output). */
+int sfseg_net_launch_shape(int kernel, int* frames, int* rows, int* ctas);
+
 /* One AdamW step (decoupled weight decay) with the gradients of the last sfseg_net_backward. */
 int sfseg_net_adamw(sfseg_net* net, float lr, float beta1, float beta2, float eps,
                     float weight_decay, void* stream);

@@ -1097,6 +1097,13 @@ int ensure_ws(sfseg_net* n, int64_t N, bool train) {
     return SFSEG_OK;
 }
 
+// The launch shape of the calling thread's most recent launch of each convolution kernel
+// (0: conv3d_tc, 1: conv_last_tc), for sfseg_net_launch_shape.
+struct LaunchShape {
+    int frames, rows, ctas;
+};
+thread_local LaunchShape last_shape[2] = {{0, 0, 0}, {0, 0, 0}};
+
 template <int CIN, int COUT, int EPI, int FR>
 int launch_conv(const void* in, int T, int H, int W, const ConvArgs& a, int items, cudaStream_t s) {
     using Cf = ConvCfg<CIN, COUT, FR>;
@@ -1111,6 +1118,7 @@ int launch_conv(const void* in, int T, int H, int W, const ConvArgs& a, int item
     k<<<items, Cf::NTHR, Cf::SMEM, s>>>(m, a);
     count_launches(1);
     NET_CUDA(cudaGetLastError());
+    last_shape[0] = {FR, a.HR, items};
     return SFSEG_OK;
 }
 
@@ -1157,6 +1165,7 @@ int launch_last(const __nv_bfloat16* in, int T, int H, int W, const LastArgs& a,
     conv_last_tc<FR><<<items, L::NTHR, L::SMEM, s>>>(m, a);
     count_launches(1);
     NET_CUDA(cudaGetLastError());
+    last_shape[1] = {FR, a.HR, items};
     return SFSEG_OK;
 }
 
@@ -1482,6 +1491,15 @@ int sfseg_net_layer_backward(sfseg_net* n, int layer, const void* in, const void
 int sfseg_net_check(sfseg_net* n, void* stream) {
     if (!n) return nfail(SFSEG_ERR_INVALID_ARG, "null net");
     return check_flags(n, (cudaStream_t)stream);
+}
+
+int sfseg_net_launch_shape(int kernel, int* frames, int* rows, int* ctas) {
+    if (kernel < 0 || kernel > 1) return nfail(SFSEG_ERR_INVALID_ARG, "kernel must be 0 or 1");
+    if (!frames || !rows || !ctas) return nfail(SFSEG_ERR_INVALID_ARG, "null output");
+    *frames = last_shape[kernel].frames;
+    *rows = last_shape[kernel].rows;
+    *ctas = last_shape[kernel].ctas;
+    return SFSEG_OK;
 }
 
 int sfseg_net_adamw(sfseg_net* n, float lr, float beta1, float beta2, float eps, float weight_decay, void* stream) {

@@ -89,6 +89,7 @@ SIGNATURES = {
     "sfseg_net_layer_forward": [_vp, _i, _vp, _i, _i, _i, _vp, _vp, _vp],
     "sfseg_net_layer_backward": [_vp, _i, _vp, _vp, _i, _i, _i, _vp, _vp, _vp, _vp],
     "sfseg_net_check": [_vp, _vp],
+    "sfseg_net_launch_shape": [_i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)],
     "sfseg_warmstart": [_vp, _vp, _vp, _i, _vp, _vp, _vp],
     "sfseg_power_iterate_noalloc": [ctypes.POINTER(Params), _i, _i, _i, _i, _vp, _i, _fp, _f,
                                     ctypes.POINTER(Neighborhood), _i, _vp, _i, _dp, _vp],
@@ -529,6 +530,14 @@ def kernel_launches() -> int:
     n = ctypes.c_int64()
     _check(lib().sfseg_kernel_launches(ctypes.byref(n)))
     return n.value
+
+
+def net_launch_shape(kernel: int):
+    """(output frames per CTA, output rows per CTA, CTAs) of this thread's most recent launch of
+    the network's hidden-layer convolution kernel (kernel 0) or of its last layer's (kernel 1)."""
+    f, r, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().sfseg_net_launch_shape(kernel, ctypes.byref(f), ctypes.byref(r), ctypes.byref(c)))
+    return f.value, r.value, c.value
 
 
 def iterate_kernel_stats():

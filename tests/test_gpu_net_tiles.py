@@ -1,17 +1,22 @@
-"""The warm-start network at the tile heights its production launches use.
+"""The warm-start network at the tile heights and frame groups its production launches use.
 
-Each convolution launch takes the tallest of 64, 32 or 16 output rows per CTA that still gives
-the grid four waves.  The small network tests select 16 rows; the volumes here select 64 rows
-(8 x 1024 x 640, as the 120 x 1080 x 1920 inference does) and 32 rows (32 x 256 x 512, the
-profiled case).  Every layer alone is compared with the FP64 oracle's plain convolution loops on
-the GPU layer's own bf16 input, so that only the fp32 accumulation and the final bf16 rounding
-differ: |gpu - ref| <= 2^-8 |ref| + 1e-5 sum|w x| (bf16's unit roundoff on the stored output,
-and an fp32-accumulation bound relative to the sum of the absolute products).  The sampled
-voxels include the tile seams along h and w, the rows where the accumulator ring in tensor
-memory wraps (every 16 rows of a tile for 32 output channels, every 32 for 16) and the volume's
-faces.  The data gradient (flipped taps, ReLU mask) is checked the same way, the weight gradient
-over a whole smaller volume, and the whole network at sampled voxels on the 9 x 9 x 9 crop
-around each (one voxel's output depends on nothing else).
+Each hidden-layer convolution launch takes three output frames per CTA when that grid still
+gives four waves at some tile height, else two, else one, and then the tallest of 64, 32 or 16
+output rows per CTA that gives four waves; the last layer's kernel takes four frames or one.
+The small network tests select one frame and 16 rows; the volumes here select three frames and
+64 rows (as the 120 x 1080 x 1920 inference does), three frames and 32 rows, three frames and
+16 rows (32 x 256 x 512, the profiled case), two frames and one frame per CTA, and frame counts
+that leave the last group of a layer short.  Each case checks the shape that the library
+reports for its launches.  Every layer alone is compared with the FP64 oracle's plain
+convolution loops on the GPU layer's own bf16 input, so that only the fp32 accumulation and the
+final bf16 rounding differ: |gpu - ref| <= 2^-8 |ref| + 1e-5 sum|w x| (bf16's unit roundoff on
+the stored output, and an fp32-accumulation bound relative to the sum of the absolute
+products).  The sampled voxels include the tile seams along h and w, rows around the wraps of
+the accumulator ring in tensor memory (5, 8 or 16 row blocks per output frame for three, two or
+one frames per CTA; 8 or 16 in the last layer), every frame position inside a CTA's group, and
+the volume's faces.  The data gradient (flipped taps, ReLU mask) is checked the same way, the
+weight gradient over a whole smaller volume, and the whole network at sampled voxels on the
+9 x 9 x 9 crop around each (one voxel's output depends on nothing else).
 """
 import numpy as np
 import pytest
@@ -35,30 +40,29 @@ def sf():
     return sfseg
 
 
-def _conv_launch(T, H, W):
-    """(output frames, output rows) per CTA that the convolution launch picks for this volume
-    (see net.cu): three frames when that grid still gives 4 waves at some tile height, else two,
-    else one."""
-    nsm = torch.cuda.get_device_properties(0).multi_processor_count
-    for fr in (3, 2, 1):
-        for hr in (64, 32, 16):
-            if -(-T // fr) * -(-W // 128) * -(-H // hr) >= 4 * nsm:
-                return fr, hr
-    return 1, 16
+def _ctas(T, H, W, frames, rows, tile_w):
+    return -(-T // frames) * -(-W // tile_w) * -(-H // rows)
 
+
+def _check_launch(sf, kernel, T, H, W, frames, rows):
+    """The library's report of its most recent launch of a convolution kernel (0: hidden layers,
+    128-voxel tiles; 1: the last layer, 126-voxel tiles) has the frames and rows per CTA that the
+    test case is meant to exercise, and one CTA per (frame group, tile column, row tile)."""
+    tile_w = 128 if kernel == 0 else 126
+    assert sf.net_launch_shape(kernel) == (frames, rows, _ctas(T, H, W, frames, rows, tile_w))
 
 
 def _points(T, H, W, HR, seed, n_random=40):
     hs = {0, 1, H - 2, H - 1}
     for base in (HR, 2 * HR, (H // HR - 1) * HR):      # tile seams along h
         hs.update({base - 1, base, base + 1})
-    for j in (1, 2, 7, 8, 9, 10, 15, 16, 17, 31, 32, 33):   # ring wraps (rings of 8 and 16 blocks)
+    for j in (1, 2, 4, 5, 6, 7, 8, 9, 10, 11, 15, 16, 17, 31, 32, 33):   # ring wraps (5, 8, 16 blocks)
         hs.add(HR + j)
     # 128-voxel tiles of the hidden layers, 126-voxel tiles of the last layer
     ws = {0, 1, 125, 126, 127, 128, 129, 251, 252, 255, 256, W - 129, W - 128, W - 2, W - 1}
     pts = set()
-    # frames 0..3 take every position inside a CTA's group of frames (two per CTA in the hidden
-    # layers, four in the last layer)
+    # frames 0..3 take every position inside a CTA's group of frames (up to three per CTA in the
+    # hidden layers, four in the last layer)
     for h in hs:
         for t in (0, 1, 2, 3, T // 2, T - 1):
             for w in (0, 125, 126, 127, 128, W - 1):
@@ -127,19 +131,6 @@ def _input16(T, H, W, seed):
     return x
 
 
-def _last_launch(T, H, W):
-    """(output frames, output rows) per CTA of the last layer's kernel (126-voxel tiles): four
-    frames when that grid gives 4 waves at one CTA per SM, else one frame, two CTAs per SM."""
-    nsm = torch.cuda.get_device_properties(0).multi_processor_count
-    for hr in (64, 32, 16):
-        if -(-T // 4) * -(-W // 126) * -(-H // hr) >= 4 * nsm:
-            return 4, hr
-    for hr in (64, 32, 16):
-        if T * -(-W // 126) * -(-H // hr) >= 8 * nsm:
-            return 1, hr
-    return 1, 16
-
-
 @pytest.mark.parametrize("shape,fr,hr,last", [((35, 1024, 640), 3, 64, (4, 64)), ((17, 1024, 640), 3, 32, (4, 32)),
                                              ((32, 256, 512), 3, 16, (4, 16)), ((5, 1024, 512), 2, 16, (4, 16)),
                                              ((2, 1024, 640), 1, 16, (1, 16))],
@@ -152,12 +143,12 @@ def test_layers_at_production_tile_heights(sf, shape, fr, hr, last):
     frames (35 = 11 x 3 + 2 and 8 x 4 + 3; 17 = 5 x 3 + 2; 5 = 2 x 2 + 1); the 2-frame volume
     runs one output frame per CTA in both kernels."""
     T, H, W = shape
-    assert _conv_launch(T, H, W) == (fr, hr)
-    assert _last_launch(T, H, W) == last
     net = sf.WarmStartNet(C_IN, seed=11)
     params = _layer_params(net)
     x16 = _input16(T, H, W, 900 + hr)
     ins, z, x0 = _forward_layers(net, x16)
+    _check_launch(sf, 0, T, H, W, fr, hr)
+    _check_launch(sf, 1, T, H, W, *last)
     pts = sorted(set(_points(T, H, W, hr, seed=hr)) | set(_points(T, H, W, last[1], seed=hr + 1, n_random=0)))
     outs = [ins[1], ins[2], ins[3], z]
     for layer in range(4):
@@ -175,7 +166,6 @@ def test_data_gradient_at_production_tile_heights(sf, shape, fr, hr):
     """dx = conv^T(dz) * [x > 0] of layers 1..3 (the data-gradient convolution on the tensor
     cores) at sampled voxels against the oracle's reverse loops on the same bf16 inputs."""
     T, H, W = shape
-    assert _conv_launch(T, H, W) == (fr, hr)
     net = sf.WarmStartNet(C_IN, seed=12)
     params = _layer_params(net)
     ins, _, _ = _forward_layers(net, _input16(T, H, W, 910 + hr))
@@ -190,6 +180,7 @@ def test_data_gradient_at_production_tile_heights(sf, shape, fr, hr):
             dz = torch.randn((T, H, W, 32), device="cuda", generator=gen).to(torch.bfloat16)
         dx, _, _ = net.layer_backward(layer, x, dz)
         net.check()
+        _check_launch(sf, 0, T, H, W, fr, hr)
         wt, _ = params[layer]
         cout = wt.shape[0]
         for p in pts:
@@ -267,7 +258,6 @@ def test_network_sampled_at_production_tile_heights(sf, shape, fr, hr):
     oracle's FP64 network on the 9 x 9 x 9 crop around each voxel, within the end-to-end bf16
     tolerance of the small network test (three hidden activations rounded to bf16)."""
     T, H, W = shape
-    assert _conv_launch(T, H, W) == (fr, hr)
     gen = torch.Generator(device="cuda").manual_seed(940 + hr)
     feats = torch.rand((8, T, H, W), device="cuda", generator=gen).to(torch.bfloat16)
     extra = torch.rand((T, H, W), device="cuda", generator=gen)
@@ -275,6 +265,7 @@ def test_network_sampled_at_production_tile_heights(sf, shape, fr, hr):
     params = _layer_params(net)
     x0 = net.forward(feats, extra)
     net.check()
+    _check_launch(sf, 0, T, H, W, fr, hr)
     extra_b = extra.to(torch.bfloat16)
     pts = _points(T, H, W, hr, seed=200 + hr, n_random=10)[::3]
     refs, gots = [], []
