@@ -434,16 +434,25 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
 // -------------------------------------------------------------- last layer (32 -> 1, tcgen05)
 // The last layer has one output channel.  Stacking its three h-taps along N as the other layers
 // do would compute 16 padded outputs per tap; here the nine (dh, dw) taps of a frame offset
-// are the N dimension instead: for input row i (one h) and voxel v along w,
-//   D_i[v, 3 dh + dw] = sum_{dt, ci} x[t + dt - 1, i, v, ci] W[dt, dh, dw, ci]     (N = 9 -> 16)
-// six MMAs per input row (3 frames x 2 channel halves, M = 128 voxels, K = 16 channels), into
-// a ring of 16-column TMEM blocks, one per input row.  Output row j (input rows j, j+1, j+2 =
-// h - 1, h, h + 1) then takes z[w] = b + sum_{dh, dw} D_{j+dh}[w + dw - 1, 3 dh + dw]: the epilogue
-// sums the three rows in each lane, exchanges the three dw sums through shared memory (a lane's
-// neighbours along w may sit in another warp) and adds them.  M = 128 voxels cover 126 outputs
-// and their w halo, so the tiles are 126 voxels wide.
+// are the N dimension instead: for input row i (one h), voxel v along w and output frame t,
+//   D_{t,i}[v, 3 dh + dw] = sum_{dt, ci} x[t + dt - 1, i, v, ci] W[dt, dh, dw, ci]   (9 -> 16 columns)
+// into a ring of TMEM blocks, one 16-column block per input row and output frame.  An input
+// frame s of the CTA's slot feeds output frames s - dt + 1 for dt = 0, 1, 2, so one MMA per input
+// frame and channel half (M = 128 voxels, K = 16 channels) covers the blocks of all FR output
+// frames of a row at once (N = 16 FR): its B operand stacks, for output frame q, the taps of
+// frame offset dt = s - q, or zeros where s - q is outside 0..2.  The taps are packed as
+// [Z Z Z W2 W1 W0 Z Z Z] (16-row blocks along N, Z zero), so that the B of slot frame s is the FR
+// blocks from block 5 - s on, and the first MMA of a row (slot frame 0) also clears the blocks
+// of the other output frames.  Per input row that is 2 (FR + 2) MMAs instead of 6 FR.  Output row
+// j (input rows j, j+1, j+2 = h - 1, h, h + 1) then takes
+// z[w] = b + sum_{dh, dw} D_{j+dh}[w + dw - 1, 3 dh + dw]: the epilogue sums the three rows in
+// each lane, exchanges the three dw sums through shared memory (a lane's neighbours along w may
+// sit in another warp) and adds them.  M = 128 voxels cover 126 outputs and their w halo, so the
+// tiles are 126 voxels wide.
 constexpr int LT_W = MT - 2;                 // outputs per tile along w
-constexpr int LT_BBYTES = 3 * 2 * 2 * 16 * 16;   // [dt][ks][chunk][16 taps][8 channels] bf16
+constexpr int LT_NBLK = 9;                   // 16-row tap blocks along N: Z Z Z W2 W1 W0 Z Z Z
+constexpr int LT_CH = LT_NBLK * 16 * 16;     // one 8-channel chunk of the taps (2304 bytes)
+constexpr int LT_BBYTES = 2 * 2 * LT_CH;     // [ks][chunk][9 x 16 taps][8 channels] bf16
 
 struct LastArgs {
     int T, H, W, HR;
@@ -455,10 +464,10 @@ struct LastArgs {
 };
 
 // FR output frames per CTA from input slots of FR + 2 frames (each output frame reads three of
-// them): the input bytes copied per output voxel fall from 3 x 64 to (FR + 2) / FR x 64.  Each
-// output frame has its own ring of R TMEM blocks, one per input row, and its own four epilogue
-// warps.  One frame per CTA (a ring of 16 blocks in 256 columns, two CTAs per SM) serves volumes
-// too small for the four-frame grid.
+// them): the input bytes copied per output voxel fall from 3 x 64 to (FR + 2) / FR x 64.  The
+// ring holds R rows; a row's FR blocks (one per output frame) are adjacent, and each output
+// frame has its own four epilogue warps.  One frame per CTA (a ring of 16 blocks in 256 columns,
+// two CTAs per SM) serves volumes too small for the four-frame grid.
 template <int FR>
 struct LastCfg {
     static constexpr int NF = FR + 2;                     // frames per input slot
@@ -467,7 +476,7 @@ struct LastCfg {
     static constexpr int SLOT = 4 * CHUNK;                // one input row: 4 chunks of 8 channels
     static constexpr int CTAS = FR == 1 ? 2 : 1;          // CTAs per SM
     static constexpr int COLS = 512 / CTAS;               // TMEM columns of the CTA
-    static constexpr int R = COLS / (16 * FR);            // blocks in one output frame's ring
+    static constexpr int R = COLS / (16 * FR);            // rows in the ring (FR blocks each)
     static constexpr int NS = NSLOT;                      // input-row slots
     static constexpr int NTHR = 32 * (2 + 4 * FR);        // producer, issuer, 4 epilogue warps per frame
     // per frame: the dw sums of two rows and each epilogue warp's wait status (double buffer)
@@ -549,10 +558,10 @@ conv_last_tc(const __grid_constant__ CUtensorMap xin, LastArgs a) {
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {   // ---------------- MMA issuer: six MMAs per input row and output frame
+        if (lane == 0) {   // ---------------- MMA issuer: 2 (FR + 2) MMAs per input row
             bool ok = mb_wait(wbar, 0, a.flags);
             const uint32_t wbase = su32(wsm), rbase = su32(ring);
-            constexpr uint32_t ID = idesc_bf16(16);
+            constexpr uint32_t ID = idesc_bf16(16 * FR);
             for (int i = 0; ok && i < nin; ++i) {
                 ok = mb_wait(&full[i % L::NS], (uint32_t)((i / L::NS) & 1), a.flags);
                 // the blocks of row i: read back by every output row of row i - R
@@ -562,23 +571,16 @@ conv_last_tc(const __grid_constant__ CUtensorMap xin, LastArgs a) {
                 if (!ok) break;
                 tc_fence_after();
                 const uint64_t a0 = sdesc(rbase + (uint32_t)((i % L::NS) * L::SLOT), L::CHUNK, 128);
-                auto frame = [&](int q) {   // output frame t0 + q reads slot frames q, q + 1, q + 2
-                    const uint32_t d = tmem + (uint32_t)((q * L::R + i % L::R) * 16);
+                // row i's blocks of all FR output frames (those past the last frame are not read)
+                const uint32_t d = tmem + (uint32_t)((i % L::R) * FR * 16);
 #pragma unroll
-                    for (int dt = 0; dt < 3; ++dt)
+                for (int sf = 0; sf < L::NF; ++sf)   // slot frame t0 - 1 + sf
 #pragma unroll
-                        for (int ks = 0; ks < 2; ++ks) {
-                            const uint64_t ad = a0 + (uint64_t)((2 * ks * L::CHUNK + (q + dt) * RW * 16) >> 4);
-                            const uint64_t bd = sdesc(wbase + (uint32_t)((dt * 2 + ks) * 512), 256, 128);
-                            umma(d, ad, bd, ID, (dt | ks) ? 1u : 0u);
-                        }
-                };
-                if (nfr == FR) {   // all frames: one branch-free run of MMAs
-#pragma unroll
-                    for (int q = 0; q < FR; ++q) frame(q);
-                } else {
-                    for (int q = 0; q < nfr; ++q) frame(q);
-                }
+                    for (int ks = 0; ks < 2; ++ks) {
+                        const uint64_t ad = a0 + (uint64_t)((2 * ks * L::CHUNK + sf * RW * 16) >> 4);
+                        const uint64_t bd = sdesc(wbase + (uint32_t)(2 * ks * LT_CH + (5 - sf) * 256), LT_CH, 128);
+                        umma(d, ad, bd, ID, (sf | ks) ? 1u : 0u);
+                    }
                 umma_commit(&empty[i % L::NS]);
                 for (int q = 0; q < nfr; ++q) umma_commit(&accf[q * L::R + i % L::R]);
             }
@@ -600,7 +602,7 @@ conv_last_tc(const __grid_constant__ CUtensorMap xin, LastArgs a) {
             ok = ok && mb_wait(&af[r % L::R], (uint32_t)((r / L::R) & 1), a.flags);
             tc_fence_after();
             uint32_t v[16];
-            tmem_ld<16>(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)((g * L::R + r % L::R) * 16), v);
+            tmem_ld<16>(tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(((r % L::R) * FR + g) * 16), v);
             tmem_ld_wait();
             tc_fence_before();
             __syncwarp();
@@ -650,18 +652,20 @@ conv_last_tc(const __grid_constant__ CUtensorMap xin, LastArgs a) {
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(L::COLS) : "memory");
 }
 
-// Taps of the last layer for conv_last_tc: out[((dt * 2 + ks) * 2 + chunk) * 16 + n][e] =
-// W[0][9 dt + 3 dh + dw][16 ks + 8 chunk + e] for n = 3 dh + dw < 9, zero for n >= 9.
+// Taps of the last layer for conv_last_tc: out[((ks * 2 + chunk) * 9 + blk) * 16 + n][e] =
+// W[0][9 dt + 3 dh + dw][16 ks + 8 chunk + e] for blk = 5 - dt (dt = 0, 1, 2) and n = 3 dh + dw < 9,
+// zero for n >= 9 and for the blocks 0..2 and 6..8.
 __global__ void pack_last_taps(const float* W, __nv_bfloat16* out) {
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < LT_BBYTES / 2; idx += gridDim.x * blockDim.x) {
         int r = idx;
         const int e = r % 8; r /= 8;
         const int n = r % 16; r /= 16;
+        const int blk = r % LT_NBLK; r /= LT_NBLK;
         const int ch = r % 2; r /= 2;
-        const int ks = r % 2; r /= 2;
-        const int dt = r;
+        const int ks = r;
+        const int dt = 5 - blk;
         float v = 0.f;
-        if (n < 9) v = W[(9 * dt + n) * 32 + ks * 16 + ch * 8 + e];
+        if (n < 9 && dt >= 0 && dt <= 2) v = W[(9 * dt + n) * 32 + ks * 16 + ch * 8 + e];
         out[idx] = __float2bfloat16_rn(v);
     }
 }
