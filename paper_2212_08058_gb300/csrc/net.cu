@@ -3,7 +3,8 @@
 // from a uniform vector or from S_m, Alg. 1 line 3; the network is an addition to the method.)
 //
 //   L1: C_in (<= 16, zero-padded to 16) -> 32, ReLU      L2, L3: 32 -> 32, ReLU
-//   L4: 32 -> 1, softplus (its own kernel, conv_last_tc: the nine (dh, dw) taps on N)
+//   L4: 32 -> 1, softplus (its own kernel, conv_last_tc: the nine (dh, dw) taps of each output
+//       frame on N)
 //
 // Activations are bf16 in channels-last layout [T][H][W][C]; every convolution is an implicit
 // GEMM on the 5th-generation tensor cores (tcgen05.mma, kind::f16, bf16 x bf16 -> fp32 in TMEM):
@@ -177,7 +178,7 @@ struct ConvArgs {
 // The three taps along h of one (dt, dw, ks) share one MMA: an input row h' feeds the output
 // rows h' + 1, h', h' - 1 through the weights of dh = 0, 1, 2, so B stacks the three weight
 // blocks along N (N = 3 COUT) and D spans the accumulators of three output rows.  Each output
-// frame of the CTA has a ring of R blocks of COUT columns in its half of the TMEM columns;
+// frame of the CTA has a ring of R blocks of COUT columns in its share of the TMEM columns;
 // output row j uses block (-j) mod R, so the rows i, i - 1, i - 2 fed by input row i sit in
 // consecutive blocks (an MMA is split in two where the ring wraps, and trimmed at the tile's
 // first and last rows).  A block is zeroed when its row has been read, so every MMA accumulates.
@@ -233,7 +234,7 @@ conv3d_tc(const __grid_constant__ CUtensorMap xin, ConvArgs a) {
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + C::NB);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // work item: (pair of frames, w segment, row range)
+    // work item: (group of up to FR output frames, w segment, row range)
     const int HR = a.HR;
     const int nws = (a.W + MT - 1) / MT, nhr = (a.H + HR - 1) / HR;
     int item = blockIdx.x;
