@@ -69,6 +69,12 @@ def test_argument_checks_without_gpu(libpath):
     assert L.sfseg_online_create(ctypes.byref(ok), 1, 0, 8, 8, ctypes.byref(o)) == 1     # q < 1
     assert L.sfseg_online_push(None, None, 0, None, 0.0, ctypes.byref(nb), 1, 0, 0, None, None) == 1
     assert L.sfseg_online_destroy(None) == 0
+    # the network's launch-shape report: nothing launched yet on this thread, bad kernel index
+    f, r, c = ctypes.c_int(-1), ctypes.c_int(-1), ctypes.c_int(-1)
+    assert L.sfseg_net_launch_shape(0, ctypes.byref(f), ctypes.byref(r), ctypes.byref(c)) == 0
+    assert (f.value, r.value, c.value) == (0, 0, 0)
+    assert L.sfseg_net_launch_shape(2, ctypes.byref(f), ctypes.byref(r), ctypes.byref(c)) == 1
+    assert L.sfseg_net_launch_shape(1, None, ctypes.byref(r), ctypes.byref(c)) == 1
 
 
 def test_binding_refuses_without_library(tmp_path, monkeypatch):
